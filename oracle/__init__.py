@@ -1,0 +1,255 @@
+"""Python face of the CPU oracle (`rtsdf_oracle.c`).
+
+TEST INFRASTRUCTURE ONLY: imported by `tests/`, `__graft_entry__.smoke()` and the
+CPU-baseline leg of `bench.py`, never by the library.  It compiles the plain C
+oracle with gcc on first use and wraps each step with numpy arrays.  The step
+functions follow the paper's order: voxelize (Sec. 2.2) -> jump flood (Sec. 2.2)
+-> coarse distance and ray mask (Sec. 2.2-2.3) -> ray-sampled refinement
+(Sec. 2.1) -> signed field -> soft-shadow raymarch (Sec. 2.4, 2.5.2-2.5.3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_DIR = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_DIR, "rtsdf_oracle.c")
+_LIB = os.path.join(_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EMPTY = -1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (FP32 without contraction, OpenMP over independent voxels)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_DIR, "rtsdf_oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                               "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("ox", C.c_float), ("oy", C.c_float), ("oz", C.c_float), ("h", C.c_float)]
+
+
+def _g(grid) -> _Grid:
+    return _Grid(grid.nx, grid.ny, grid.nz, *[float(v) for v in grid.origin], float(grid.h))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            f32, i32, i64, u32 = C.c_float, C.c_int32, C.c_int64, C.c_uint32
+            G = C.POINTER(_Grid)
+            sig = {
+                "or_to_voxel": (None, [P, i32, G, P]),
+                "or_tri_box_overlap": (C.c_int, [P, P, P, f32, f32, f32, f32]),
+                "or_closest_d2": (f32, [P, P, P, P]),
+                "or_voxelize": (i32, [P, i32, P, i32, G, P, P]),
+                "or_jfa_pass": (None, [G, P, i32, P]),
+                "or_resolve": (None, [G, P, P, P, P, f32, f32, P, P]),
+                "or_philox4x32_10": (None, [P, P, P]),
+                "or_sphere_dir": (C.c_int, [u32, u32, u32, P, P]),
+                "or_ray_tri": (C.c_int, [P, P, P, P, P, f32, P, P]),
+                "or_refine_voxels": (i64, [G, P, i32, P, i32, P, i64, i32, f32, P, u32, u32, P, P, P]),
+                "or_vote_sign": (C.c_int, [u32, u32, P, P, P, P, C.c_int]),
+                "or_finalize": (None, [G, P, P, P, P, P, P, P, P, P, f32, C.c_int, P]),
+                "or_trilinear": (f32, [G, P, f32, f32, f32]),
+                "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P]),
+                "or_num_threads": (C.c_int, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+def empty_dist(grid) -> float:
+    """Coarse distance given to voxels that no seed reaches: nx + ny + nz voxels."""
+    return float(grid.nx + grid.ny + grid.nz)
+
+
+# ------------------------------------------------------------------ primitives
+
+def to_voxel(verts, grid) -> np.ndarray:
+    v = _f32(verts)
+    out = np.empty_like(v)
+    lib().or_to_voxel(_p(v), len(v), C.byref(_g(grid)), _p(out))
+    return out
+
+
+def tri_box_overlap(a, b, c, centre, hs: float) -> bool:
+    a, b, c = _f32(a), _f32(b), _f32(c)
+    return bool(lib().or_tri_box_overlap(_p(a), _p(b), _p(c), float(centre[0]), float(centre[1]),
+                                         float(centre[2]), float(hs)))
+
+
+def closest_d2(p, a, b, c) -> float:
+    p, a, b, c = _f32(p), _f32(a), _f32(b), _f32(c)
+    return float(lib().or_closest_d2(_p(p), _p(a), _p(b), _p(c)))
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def sphere_dir(voxel: int, ray: int, scene: int, key) -> tuple[np.ndarray, int]:
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    d = np.zeros(3, dtype=np.float32)
+    att = lib().or_sphere_dir(voxel & 0xFFFFFFFF, ray & 0xFFFFFFFF, scene & 0xFFFFFFFF, _p(k), _p(d))
+    return d, att
+
+
+def ray_tri(o, d, a, b, c, tmax: float):
+    o, d, a, b, c = _f32(o), _f32(d), _f32(a), _f32(b), _f32(c)
+    t = np.zeros(1, dtype=np.float32)
+    f = np.zeros(1, dtype=np.int32)
+    hit = lib().or_ray_tri(_p(o), _p(d), _p(a), _p(b), _p(c), float(tmax), _p(t), _p(f))
+    return (bool(hit), float(t[0]), bool(f[0])) if hit else (False, None, None)
+
+
+def trilinear(grid, sdf, q) -> float:
+    s = _f32(sdf)
+    return float(lib().or_trilinear(C.byref(_g(grid)), _p(s), float(q[0]), float(q[1]), float(q[2])))
+
+
+# ------------------------------------------------------------------ the steps
+
+def voxelize(vv, tris, grid):
+    """Sec. 2.2 seeds from voxel-space vertices: (seed grid, rep-tri grid, skipped count)."""
+    vv, t = _f32(vv), _i32(tris)
+    seed = np.empty(grid.shape_zyx, dtype=np.int32)
+    rep = np.empty(grid.shape_zyx, dtype=np.int32)
+    sk = lib().or_voxelize(_p(vv), len(vv), _p(t), len(t), C.byref(_g(grid)), _p(seed), _p(rep))
+    return seed, rep, int(sk)
+
+
+def jfa_pass(grid, seeds, k: int) -> np.ndarray:
+    a = _i32(seeds)
+    out = np.empty_like(a)
+    lib().or_jfa_pass(C.byref(_g(grid)), _p(a), int(k), _p(out))
+    return out
+
+
+def jfa(grid, seeds, steps) -> np.ndarray:
+    a = _i32(seeds).copy()
+    for k in steps:
+        a = jfa_pass(grid, a, k)
+    return a
+
+
+def resolve(grid, vv, tris, nearest, rep_tri, mask_vox: float):
+    vv, t, n, r = _f32(vv), _i32(tris), _i32(nearest), _i32(rep_tri)
+    u_c = np.empty(grid.shape_zyx, dtype=np.float32)
+    mask = np.empty(grid.shape_zyx, dtype=np.uint8)
+    lib().or_resolve(C.byref(_g(grid)), _p(vv), _p(t), _p(n), _p(r), float(mask_vox),
+                     empty_dist(grid), _p(u_c), _p(mask))
+    return u_c, mask
+
+
+def refine_voxels(grid, vv, tris, vox, rp, frame: int, dist_bits, front, back) -> int:
+    """Sec. 2.1 on the listed voxels; dist_bits/front/back are updated in place."""
+    vv, t, vox = _f32(vv), _i32(tris), _i32(vox)
+    key = np.array(rp.key, dtype=np.uint32)
+    for a in (dist_bits, front, back):
+        assert a.dtype == np.uint32 and a.flags["C_CONTIGUOUS"]
+    return int(lib().or_refine_voxels(C.byref(_g(grid)), _p(vv), len(vv), _p(t), len(t), _p(vox),
+                                      len(vox), int(rp.rays_per_voxel), float(rp.max_ray_vox),
+                                      _p(key), frame & 0xFFFFFFFF, rp.scene_id & 0xFFFFFFFF,
+                                      _p(dist_bits), _p(front), _p(back)))
+
+
+def finalize(grid, vv, tris, nearest, rep_tri, mask, u_c, dist_bits, front, back, rp) -> np.ndarray:
+    sdf = np.empty(grid.shape_zyx, dtype=np.float32)
+    arrs = [_f32(vv), _i32(tris), _i32(nearest), _i32(rep_tri),
+            np.ascontiguousarray(mask, dtype=np.uint8), _f32(u_c),
+            np.ascontiguousarray(dist_bits, dtype=np.uint32),
+            np.ascontiguousarray(front, dtype=np.uint32), np.ascontiguousarray(back, dtype=np.uint32)]
+    lib().or_finalize(C.byref(_g(grid)), *[_p(a) for a in arrs], float(rp.beta_vox),
+                      int(bool(rp.sign_fallback)), _p(sdf))
+    return sdf
+
+
+def shadow(grid, sdf, pos, nrm, sp) -> np.ndarray:
+    s, pos, nrm = _f32(sdf), _f32(pos), _f32(nrm)
+    L = np.array(sp.light_dir, dtype=np.float32)
+    vis = np.empty(len(pos), dtype=np.float32)
+    lib().or_shadow(C.byref(_g(grid)), _p(s), _p(pos), _p(nrm), len(pos), _p(L), float(sp.k),
+                    int(sp.steps), float(sp.max_step_vox), float(sp.start_offset_vox),
+                    float(sp.normal_offset_vox), float(sp.hit_eps_vox), float(sp.bias_vox), _p(vis))
+    return vis
+
+
+def init_refine_state(u_c, mask, state=None, accumulate=False):
+    """Refinement state before a frame's rays: masked voxels start from the coarse
+    distance (or the smaller of it and the accumulated distance), counts from zero
+    (or the accumulated counts); unmasked voxels hold the coarse distance, no votes."""
+    d0 = u_c.view(np.uint32).copy()
+    if state is None or not accumulate:
+        return d0, np.zeros_like(d0), np.zeros_like(d0)
+    dist, fr, bk = state
+    m = mask.astype(bool)
+    dist = np.where(m, np.minimum(dist.view(np.float32), u_c).view(np.uint32), d0)
+    return (np.ascontiguousarray(dist, dtype=np.uint32), np.where(m, fr, 0).astype(np.uint32),
+            np.where(m, bk, 0).astype(np.uint32))
+
+
+def rebuild(scene, frames: int | None = None, frame0: int = 0, voxel_subset=None):
+    """Full oracle rebuild of a scene: every intermediate of the hot path.
+
+    `voxel_subset` (linear indices) restricts ray sampling to those masked voxels
+    (for large grids); the returned refine arrays are then only meaningful there.
+    """
+    g, rp = scene.grid, scene.refine
+    vv = to_voxel(scene.verts, g)
+    seed, rep, skipped = voxelize(vv, scene.tris, g)
+    nearest = jfa(g, seed, scene.jfa_steps)
+    u_c, mask = resolve(g, vv, scene.tris, nearest, rep, rp.mask_vox)
+    masked = np.flatnonzero(mask.ravel()).astype(np.int32)
+    todo = masked if voxel_subset is None else np.intersect1d(masked, voxel_subset).astype(np.int32)
+    state = None
+    nf = scene.frames if frames is None else frames
+    for f in range(nf):
+        state = init_refine_state(u_c, mask, state, accumulate=rp.accumulate)
+        dist, fr, bk = (a.ravel() for a in state)
+        refine_voxels(g, vv, scene.tris, todo, rp, frame0 + f, dist, fr, bk)
+        state = (dist.reshape(g.shape_zyx), fr.reshape(g.shape_zyx), bk.reshape(g.shape_zyx))
+    dist, fr, bk = state
+    sdf = finalize(g, vv, scene.tris, nearest, rep, mask, u_c, dist, fr, bk, rp)
+    return dict(vv=vv, seed=seed, rep_tri=rep, skipped=skipped, nearest=nearest, u_c=u_c,
+                mask=mask, masked=masked, refined=todo, dist_bits=dist, front=fr, back=bk, sdf=sdf)
