@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the RTSDF hot path on one GB300 (per rank).
+
+A step is one frame of the whole path on the paper-shaped 400x200x400 room scene
+(ground quad + 40 tessellated primitives, ~109k triangles): voxelize -> LBVH ->
+10 jump-flooding passes (256..1 plus one extra 1) -> resolve + refine with 8 rays
+per masked voxel (accumulated over frames) -> 1920x1080 soft-shadow raymarch.
+Inputs are resident in HBM when the timed region starts; the per-frame working
+set (~1.4 GB of grids) is far larger than L2, so no L2 flush is needed.
+
+  python bench.py [--steps K] [--warmup W] [--workload room|tiny] [--impl reference]
+
+Under torchrun every rank runs an independent replica (the path has no exchange
+step); value = frames of all ranks / max-over-ranks time, expressed in ms/frame.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SDF rebuild ms/frame @400x200x400, GVoxel/s, %HBM roof; bwd+batch vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="room", choices=["room", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_scene(workload: str):
+    from paper_2210_06160_gb300 import scenes
+    return scenes.scene_room() if workload == "room" else scenes.scene_tiny()
+
+
+def workload_config(sc, workload: str) -> dict:
+    g = sc.grid
+    return {"workload": ("room scene 400x200x400 (ground quad + 40 primitives), 8 rays/voxel/frame "
+                         "accumulated, 1920x1080 shadow, 96 steps" if workload == "room" else
+                         "icosphere 64^3, 16 rays/voxel, 256x256 shadow, 64 steps"),
+            "grid": [g.nx, g.ny, g.nz], "triangles": int(len(sc.tris)), "jfa_passes": len(sc.jfa_steps),
+            "rays_per_voxel": sc.refine.rays_per_voxel, "receivers": int(len(sc.recv_pos)),
+            "raymarch_steps": sc.shadow.steps,
+            "l2": "working set > L2 (grids of 128 MB each); no flush"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        for r in rows:
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6), ("sw_thermal_slowdown", 7),
+                              ("sw_power_cap", 8)):
+                if r[col].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
+    """The oracle as it stands on a bounded sample of one frame, scaled to a full
+    frame: full voxelize, 2 of the JFA passes (scaled to all), full resolve,
+    ray sampling of a subset of masked voxels (scaled to all masked voxels), and
+    the shadow of a subset of receivers (scaled to all)."""
+    import numpy as np
+
+    import oracle
+    g, rp = sc.grid, sc.refine
+    t = {}
+    t0 = time.perf_counter()
+    vv = oracle.to_voxel(sc.verts, g)
+    seed, rep, _ = oracle.voxelize(vv, sc.tris, g)
+    t["voxelize"] = time.perf_counter() - t0
+    npass = min(2, len(sc.jfa_steps))
+    t0 = time.perf_counter()
+    a = seed
+    for k in sc.jfa_steps[-npass:]:
+        a = oracle.jfa_pass(g, a, k)
+    t["jfa"] = (time.perf_counter() - t0) * len(sc.jfa_steps) / npass
+    near = oracle.jfa(g, seed, sc.jfa_steps) if sc.grid.nvox <= 64 ** 3 else a
+    t0 = time.perf_counter()
+    u_c, mask = oracle.resolve(g, vv, sc.tris, near, rep, rp.mask_vox)
+    t["resolve"] = time.perf_counter() - t0
+    masked = np.flatnonzero(mask.ravel()).astype(np.int32)
+    nsub = max(1, min(len(masked), 48 if len(sc.tris) > 10000 else 4096))
+    sub = masked[:: max(1, len(masked) // nsub)][:nsub]
+    d, f, b = (x.ravel() for x in oracle.init_refine_state(u_c, mask))
+    t0 = time.perf_counter()
+    oracle.refine_voxels(g, vv, sc.tris, sub, rp, 0, d, f, b)
+    t["refine"] = (time.perf_counter() - t0) * len(masked) / max(1, len(sub))
+    sdf = (u_c - np.float32(rp.beta_vox)).astype(np.float32)
+    npix = min(len(sc.recv_pos), 50_000)
+    t0 = time.perf_counter()
+    oracle.shadow(g, sdf, sc.recv_pos[:npix], sc.recv_nrm[:npix], sc.shadow)
+    t["shadow"] = (time.perf_counter() - t0) * len(sc.recv_pos) / npix
+    total_ms = 1e3 * sum(t.values())
+    return {"value": total_ms, "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"full voxelize + resolve; {npass} of {len(sc.jfa_steps)} JFA passes scaled; ray sampling "
+                       f"of {len(sub)} of {len(masked)} masked voxels scaled; shadow of {npix} of "
+                       f"{len(sc.recv_pos)} receivers scaled"),
+            "stage_s": {k: round(v, 3) for k, v in t.items()}}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = load_scene(args.workload)
+    for _ in range(args.warmup):
+        oracle_frame_sample(sc)
+    vals, stage = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle_frame_sample(sc)
+        vals.append(r["value"])
+        stage = r
+    wall = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms/frame", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(sc, args.workload),
+            "cpu_baseline": {"value": v, "unit": "ms/frame", "cores": stage["cores"], "kind": "oracle",
+                             "sample": stage["sample"]},
+            "e2e": {"value": v, "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 2)}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU path
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2210_06160_gb300 import build
+    from paper_2210_06160_gb300 import rtsdf as rt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    rt.lib()
+
+    sc = load_scene(args.workload)
+    g = sc.grid
+    dev = torch.device("cuda", local)
+    verts = torch.from_numpy(sc.verts).to(dev)
+    tris = torch.from_numpy(sc.tris).to(dev)
+    pos = torch.from_numpy(sc.recv_pos).to(dev)
+    nrm = torch.from_numpy(sc.recv_nrm).to(dev)
+    P = rt.Pipeline(g, len(sc.verts), len(sc.tris), device=dev)
+    vis = torch.empty(len(sc.recv_pos), dtype=torch.float32, device=dev)
+    sp = rt.make_shadow_params(sc.shadow)
+    stream = torch.cuda.current_stream()
+
+    def params(f):
+        return rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f, accumulate=f > 0))
+
+    def frame(f, ev=None):
+        if ev:
+            ev[0].record()
+        P.voxelize(verts, tris)
+        if ev:
+            ev[1].record()
+        P.build_bvh(verts, tris)
+        if ev:
+            ev[2].record()
+        P.jfa(sc.jfa_steps)
+        if ev:
+            ev[3].record()
+        P.refine(verts, tris, params(f))
+        if ev:
+            ev[4].record()
+        P.shadow(pos, nrm, sp, vis)
+        if ev:
+            ev[5].record()
+
+    f = 0
+    for _ in range(args.warmup):
+        frame(f)
+        f += 1
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    n_launch0 = rt.rtsdf_kernel_launches()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    start.record(stream)
+    for i in range(args.steps):
+        frame(f, evs[i])
+        f += 1
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = rt.rtsdf_kernel_launches() - n_launch0
+    clk = clocks.stop()
+    t_ms = start.elapsed_time(end)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    names = ["voxelize", "bvh", "jfa", "refine", "shadow"]
+    stage = {n: statistics.mean(evs[i][j].elapsed_time(evs[i][j + 1]) for i in range(args.steps))
+             for j, n in enumerate(names)}
+    ms_per_step = t_ms / args.steps
+    frames_all = args.steps * world
+    value = t_ms / frames_all
+    rebuild_ms = stage["voxelize"] + stage["bvh"] + stage["jfa"] + stage["refine"]
+    nvox = g.nvox
+
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak_src = "measured"
+    try:
+        hbm_peak = float(json.load(open(peaks_path))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm_peak, peak_src = 6800.0, "fallback"
+    jfa_bytes = 8.0 * nvox * len(sc.jfa_steps)  # 4 B read + 4 B write per voxel per pass
+    jfa_gbs = jfa_bytes / (stage["jfa"] * 1e-3) / 1e9
+    roofline = {"kernel": "k_jfa_pass (all passes of a frame)", "bound": "hbm", "achieved": round(jfa_gbs, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(jfa_gbs / hbm_peak, 4), "traffic": None,
+                "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes}
+
+    counters = rt.counters_dict(P.counters)
+
+    # end to end through the C-ABI with host buffers: H2D of the mesh, D2H of sdf + visibility
+    e2e = None
+    if not args.no_e2e:
+        h_verts = torch.from_numpy(sc.verts).pin_memory()
+        h_tris = torch.from_numpy(sc.tris).pin_memory()
+        h_sdf = torch.empty(P.sdf.shape, dtype=torch.float32).pin_memory()
+        h_vis = torch.empty(vis.shape, dtype=torch.float32).pin_memory()
+        ke = max(3, min(args.steps, 10))
+
+        def e2e_frame(fi):
+            verts.copy_(h_verts, non_blocking=True)
+            tris.copy_(h_tris, non_blocking=True)
+            frame(fi)
+            h_sdf.copy_(P.sdf, non_blocking=True)
+            h_vis.copy_(vis, non_blocking=True)
+
+        for _ in range(2):
+            e2e_frame(f)
+            f += 1
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_frame(f)
+            f += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([te], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": te / (ke * world), "unit": "ms/frame",
+               "h2d_bytes_per_step": int(h_verts.numel() * 4 + h_tris.numel() * 4),
+               "d2h_bytes_per_step": int(h_sdf.numel() * 4 + h_vis.numel() * 4), "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_frame_sample(sc)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "ms/frame", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload_config(sc, args.workload),
+                "gvoxel_per_s": round(nvox / (rebuild_ms * 1e-3) / 1e9, 3),
+                "rebuild_ms": round(rebuild_ms, 4),
+                "stage_ms": {k: round(v, 4) for k, v in stage.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk, "counters": counters, "impl": "ours"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    del np
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

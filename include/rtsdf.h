@@ -1,0 +1,197 @@
+/*
+ * rtsdf.h -- C-ABI of librtsdf, a GB300 (sm_103a) implementation of the per-frame
+ * signed-distance-field rebuild and soft-shadow raymarch of RTSDF (Tan, Chua,
+ * Koh, Bhojan: "RTSDF: Real-time Signed Distance Fields for Soft Shadow
+ * Approximation in Games").
+ *
+ * Pipeline per frame (Sec. 2): conservative voxelization of the triangle scene
+ * into a seed grid (rtsdf_voxelize) -> 3D jump flooding of nearest seeds
+ * (rtsdf_jfa) -> ray-sampled refinement of voxels close to a surface, with
+ * a device-built BVH (rtsdf_build_bvh, rtsdf_refine) -> sphere-traced soft shadow
+ * on the resulting field (rtsdf_shadow).
+ *
+ * Conventions shared by every call
+ *  - Grid: nx*ny*nz voxels (each dimension 1..1023) of edge h, min corner origin;
+ *    linear index (k*ny + j)*nx + i, x fastest.  World point v maps to voxel
+ *    coordinates (v - origin)/h, so voxel (i,j,k) has its centre at (i+.5,j+.5,k+.5).
+ *    Distances in parameters and outputs are in voxel units.
+ *  - Packed seed: (k << 20) | (j << 10) | i; RTSDF_EMPTY (-1) = no seed.
+ *  - Meshes: float32 vertices [V][3] (world), int32 triangles [T][3], counter-
+ *    clockwise seen from outside.  Triangles with an index outside [0, V) or a
+ *    non-finite vertex are skipped by every call (and counted).
+ *  - Memory: every pointer argument is DEVICE memory owned by the caller unless
+ *    stated otherwise; the library never allocates, frees or synchronises.  Work
+ *    is enqueued on `stream` (NULL = legacy default stream).  Workspaces are
+ *    caller-allocated, sized by the matching *_workspace query, 256-byte aligned.
+ *  - Errors: return codes only.  Argument errors are reported before anything is
+ *    enqueued (RTSDF_EINVAL / RTSDF_ENOMEM); launch failures as RTSDF_ECUDA.
+ *    Device-side conditions (skipped triangles, traversal-stack overflow, rays
+ *    whose direction could not be drawn) are counted in an optional rtsdf_counters
+ *    block in device memory that the caller zeroes and reads back.
+ *  - Determinism: every output is independent of scheduling; integer outputs are
+ *    bit-exact against the plain definitions (no FMA contraction, correctly
+ *    rounded division and square root).
+ */
+#ifndef RTSDF_H
+#define RTSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* rtsdf_stream;
+
+#define RTSDF_EMPTY (-1)
+#define RTSDF_MAX_DIM 1023
+
+typedef enum {
+    RTSDF_OK = 0,
+    RTSDF_EINVAL = 1, /* invalid argument (null or misaligned pointer, bad size or parameter) */
+    RTSDF_ENOMEM = 2, /* caller-provided workspace or buffer smaller than required */
+    RTSDF_ECUDA = 3   /* a CUDA launch or runtime call failed */
+} rtsdf_status;
+
+typedef struct {
+    int32_t nx, ny, nz; /* voxels per axis, 1..1023 */
+    float origin[3];    /* world position of the grid's min corner */
+    float h;            /* voxel edge in world units, > 0 */
+} rtsdf_grid;
+
+/* Ray-sampled refinement (Sec. 2.1) and ray mask (Sec. 2.3); distances in voxels. */
+typedef struct {
+    float mask_vox;         /* refine voxel v iff |v - seed(v)|^2 <= mask_vox^2 (integer seed distance) */
+    int32_t rays_per_voxel; /* R >= 1 rays per masked voxel per call */
+    float max_ray_vox;      /* a hit counts iff 0 < t <= max_ray_vox */
+    float beta_vox;         /* unmasked voxels store coarse distance - beta (Sec. 2.2 thickening) */
+    uint32_t key[2];        /* Philox4x32-10 key */
+    uint32_t frame_index;   /* ray r of this call has ray id frame_index*R + r */
+    uint32_t scene_id;      /* third Philox counter word */
+    int32_t accumulate;     /* 1: keep dist/front/back of earlier frames (Sec. 2.1 temporal accumulation) */
+    int32_t sign_fallback;  /* 1: front == back -> side of the representative triangle's plane */
+} rtsdf_refine_params;
+
+/* Soft-shadow raymarch (Sec. 2.4, 2.5.2, 2.5.3); distances in voxels. */
+typedef struct {
+    float light_dir[3];      /* direction toward the light (normalised by the library) */
+    float k;                 /* penumbra factor */
+    int32_t steps;           /* maximum samples per receiver */
+    float max_step_vox;      /* step cap (Sec. 2.5.2) */
+    float start_offset_vox;  /* first sample distance along the light direction */
+    float normal_offset_vox; /* lift of the ray origin along the receiver normal */
+    float hit_eps_vox;       /* occluded when sampled distance <= hit_eps */
+    float bias_vox;          /* subtracted from every sample (Sec. 2.5.3 thickening) */
+} rtsdf_shadow_params;
+
+/* Device-side counters; each call adds to the fields it owns. */
+typedef struct {
+    uint32_t skipped_triangles; /* voxelize / build_bvh: invalid triangles */
+    uint32_t masked_voxels;     /* refine: voxels inside the ray mask */
+    uint32_t rays_hit;          /* refine: rays with a hit */
+    uint32_t rays_failed;       /* refine: rays with no direction after 32 Philox draws */
+    uint32_t stack_overflow;    /* refine: traversals that overflowed the stack (result incomplete) */
+    uint32_t reserved[3];
+} rtsdf_counters;
+
+/* ---------------------------------------------------------------- voxelize */
+
+/* Bytes of workspace rtsdf_voxelize needs for T triangles on grid g (0 on bad args). */
+size_t rtsdf_voxelize_workspace(int32_t T, const rtsdf_grid* g);
+
+/* Sec. 2.2 (Jump Flooding): "we voxelize the scene with voxel resolution equal to
+ * our final distance field", every triangle point being a seed.  Conservative:
+ * voxel v is a seed iff some closed triangle overlaps v's closed cube (13-axis
+ * separating-axis test in FP32).  Outputs (nx*ny*nz int32 each):
+ *   seed[v]    = packed(v) for seed voxels, else RTSDF_EMPTY;
+ *   rep_tri[v] = among the triangles overlapping v, the one whose closest point is
+ *                nearest v's centre (ties -> lower triangle id); -1 elsewhere.
+ * ws >= rtsdf_voxelize_workspace(T, g).  counters may be NULL. */
+rtsdf_status rtsdf_voxelize(const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                            const rtsdf_grid* g, int32_t* seed, int32_t* rep_tri,
+                            void* ws, size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- BVH */
+
+/* Bytes of the BVH buffer and of the build workspace for T triangles. */
+size_t rtsdf_bvh_bytes(int32_t T);
+size_t rtsdf_bvh_workspace(int32_t T);
+
+/* Bounding-volume hierarchy over the mesh for the ray queries of Sec. 2.1 (the
+ * paper uses the driver-built DXR structure, Sec. 2 and 3.5.1): linear BVH from
+ * 30-bit Morton codes of triangle centroids in the grid box, radix-sorted, with
+ * Karras' (HPG 2012) radix-tree topology and bottom-up conservative boxes.  The
+ * buffer is self-contained (leaves hold voxel-space triangles) and only
+ * meaningful to rtsdf_refine with the same grid. */
+rtsdf_status rtsdf_build_bvh(const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                             const rtsdf_grid* g, void* bvh, size_t bvh_bytes,
+                             void* ws, size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- jump flooding */
+
+/* Sec. 2.2 (Jump Flooding, after Rong & Tan 2006, extended to 3D): for each
+ * offset k = steps[0], steps[1], ... every voxel v takes, among the stored seeds
+ * of the 27 voxels v + k*d, d in {-1,0,1}^3 inside the grid, the one nearest v
+ * (integer squared distance between voxel centres; ties -> lower packed seed).
+ * Passes read one buffer and write the other (Jacobi).  buf_a holds the seeds on
+ * entry; both buffers are nx*ny*nz int32.  On return *result (host pointer) names
+ * the buffer that holds the flooded field (buf_a for an even number of passes).
+ * steps: HOST array of nsteps offsets, each in 1..1023; nsteps >= 0. */
+rtsdf_status rtsdf_jfa(const rtsdf_grid* g, int32_t* buf_a, int32_t* buf_b, const int32_t* steps,
+                       int32_t nsteps, int32_t** result, rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- refine */
+
+size_t rtsdf_refine_workspace(const rtsdf_grid* g);
+
+/* Coarse field, ray mask and ray-sampled refinement of one frame.
+ *  - Coarse (Sec. 2.2-2.3): u_c(v) = distance from v's centre to rep_tri of its
+ *    flooded seed nearest(v); mask(v) iff integer |v - nearest(v)|^2 <= mask_vox^2.
+ *    Unmasked voxels get sdf_out = u_c - beta (no seed: u_c = nx+ny+nz).
+ *  - Refine (Sec. 2.1): each masked voxel shoots R rays from its centre with
+ *    directions uniform on the sphere (Philox4x32-10 on counter (voxel, ray id,
+ *    scene_id, attempt) + Marsaglia's rejection method).  The closest hit of each
+ *    ray (0 < t <= max_ray_vox, ties -> lower triangle id) lowers dist and adds a
+ *    front (ray meets the counter-clockwise side) or back vote.
+ *  - State: dist_bits (float bits), front, back are nx*ny*nz uint32, defined at
+ *    masked voxels.  accumulate = 0 starts them at (u_c, 0, 0); accumulate = 1
+ *    keeps earlier frames (dist = min(dist, u_c)).
+ *  - sdf_out (nx*ny*nz float) at masked voxels: -dist if back > front, +dist if
+ *    front > back; on a tie the side of rep_tri's plane when sign_fallback, else +.
+ * verts/tris must be the mesh the BVH and rep_tri were built from. */
+rtsdf_status rtsdf_refine(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris,
+                          int32_t T, const void* bvh, size_t bvh_bytes, const int32_t* nearest,
+                          const int32_t* rep_tri, const rtsdf_refine_params* p, uint32_t* dist_bits,
+                          uint32_t* front, uint32_t* back, float* sdf_out, void* ws, size_t ws_bytes,
+                          rtsdf_counters* counters, rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- shadow */
+
+/* Sec. 2.4 sphere tracing toward a directional light with the penumbra estimate
+ * k * e / (t - y) (Sec. 2.4; Aaltonen 2018 triangulation of the two latest samples,
+ * Sec. 2.5.2: y = d^2 / (2 d_prev), e = sqrt(d^2 - y^2)), step cap (Sec. 2.5.2),
+ * bias (Sec. 2.5.3).  The SDF is sampled trilinearly between voxel centres (clamp
+ * to edge).  Receiver i: world position pos[3i..], normal nrm[3i..] (the headless
+ * stand-in for a G-buffer).  Marching stops when the sample leaves the grid box,
+ * after `steps` samples, or when the sample is <= hit_eps (visibility 0).
+ * vis[i] in [0, 1]. */
+rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm,
+                          int32_t P, const rtsdf_shadow_params* p, float* vis, rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- misc */
+
+const char* rtsdf_status_string(rtsdf_status s);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t rtsdf_version(void);
+
+/* Number of CUDA kernels this library has enqueued in this process (all devices,
+ * all streams), for accounting of launches per frame.  Thread-safe. */
+uint64_t rtsdf_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTSDF_H */

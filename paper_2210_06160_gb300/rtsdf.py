@@ -1,0 +1,258 @@
+"""Thin Python binding of librtsdf (include/rtsdf.h).
+
+The functions carry the C-ABI names and only marshal arguments: torch CUDA
+tensors are passed as device pointers on the current torch stream, every step of
+the computation runs in the library's CUDA kernels.  PyTorch provides device
+memory and streams.  There is no fallback: if the compiled library is missing or
+no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librtsdf.so")
+
+EMPTY = -1
+MAX_DIM = 1023
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RtsdfError(RuntimeError):
+    pass
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("origin", C.c_float * 3), ("h", C.c_float)]
+
+
+class RefineParams(C.Structure):
+    _fields_ = [("mask_vox", C.c_float), ("rays_per_voxel", C.c_int32), ("max_ray_vox", C.c_float),
+                ("beta_vox", C.c_float), ("key", C.c_uint32 * 2), ("frame_index", C.c_uint32),
+                ("scene_id", C.c_uint32), ("accumulate", C.c_int32), ("sign_fallback", C.c_int32)]
+
+
+class ShadowParams(C.Structure):
+    _fields_ = [("light_dir", C.c_float * 3), ("k", C.c_float), ("steps", C.c_int32),
+                ("max_step_vox", C.c_float), ("start_offset_vox", C.c_float),
+                ("normal_offset_vox", C.c_float), ("hit_eps_vox", C.c_float), ("bias_vox", C.c_float)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("skipped_triangles", C.c_uint32), ("masked_voxels", C.c_uint32),
+                ("rays_hit", C.c_uint32), ("rays_failed", C.c_uint32),
+                ("stack_overflow", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+
+
+COUNTER_FIELDS = [f for f, _ in Counters._fields_ if f != "reserved"]
+
+_P = C.c_void_p
+_SIGS = {
+    "rtsdf_version": (C.c_int32, []),
+    "rtsdf_kernel_launches": (C.c_uint64, []),
+    "rtsdf_status_string": (C.c_char_p, [C.c_int]),
+    "rtsdf_voxelize_workspace": (C.c_size_t, [C.c_int32, C.POINTER(Grid)]),
+    "rtsdf_voxelize": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.POINTER(Grid), _P, _P, _P, C.c_size_t, _P, _P]),
+    "rtsdf_bvh_bytes": (C.c_size_t, [C.c_int32]),
+    "rtsdf_bvh_workspace": (C.c_size_t, [C.c_int32]),
+    "rtsdf_build_bvh": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.POINTER(Grid), _P, C.c_size_t, _P, C.c_size_t,
+                                  _P, _P]),
+    "rtsdf_jfa": (C.c_int, [C.POINTER(Grid), _P, _P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_void_p), _P]),
+    "rtsdf_refine_workspace": (C.c_size_t, [C.POINTER(Grid)]),
+    "rtsdf_refine": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t, _P, _P,
+                               C.POINTER(RefineParams), _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
+    "rtsdf_shadow": (C.c_int, [C.POINTER(Grid), _P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P]),
+}
+
+
+def lib() -> C.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RtsdfError(f"librtsdf.so not built ({LIB_PATH}); run `python -m paper_2210_06160_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        msg = lib().rtsdf_status_string(status).decode()
+        raise RtsdfError(f"{what} failed: {msg} ({status})")
+
+
+def _dev(t: torch.Tensor | None, dtype, name: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise RtsdfError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise RtsdfError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise RtsdfError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_grid(g) -> Grid:
+    """From any object with nx, ny, nz, origin, h (e.g. scenes.Grid)."""
+    return Grid(int(g.nx), int(g.ny), int(g.nz), (C.c_float * 3)(*[float(v) for v in g.origin]), float(g.h))
+
+
+def make_refine_params(rp) -> RefineParams:
+    return RefineParams(float(rp.mask_vox), int(rp.rays_per_voxel), float(rp.max_ray_vox), float(rp.beta_vox),
+                        (C.c_uint32 * 2)(*[int(k) & 0xFFFFFFFF for k in rp.key]), int(rp.frame_index) & 0xFFFFFFFF,
+                        int(rp.scene_id) & 0xFFFFFFFF, int(bool(rp.accumulate)), int(bool(rp.sign_fallback)))
+
+
+def make_shadow_params(sp) -> ShadowParams:
+    return ShadowParams((C.c_float * 3)(*[float(v) for v in sp.light_dir]), float(sp.k), int(sp.steps),
+                        float(sp.max_step_vox), float(sp.start_offset_vox), float(sp.normal_offset_vox),
+                        float(sp.hit_eps_vox), float(sp.bias_vox))
+
+
+# ------------------------------------------------------------ size queries
+
+def rtsdf_voxelize_workspace(T: int, grid: Grid) -> int:
+    return int(lib().rtsdf_voxelize_workspace(int(T), C.byref(grid)))
+
+
+def rtsdf_bvh_bytes(T: int) -> int:
+    return int(lib().rtsdf_bvh_bytes(int(T)))
+
+
+def rtsdf_bvh_workspace(T: int) -> int:
+    return int(lib().rtsdf_bvh_workspace(int(T)))
+
+
+def rtsdf_refine_workspace(grid: Grid) -> int:
+    return int(lib().rtsdf_refine_workspace(C.byref(grid)))
+
+
+# ------------------------------------------------------------ the calls
+
+def rtsdf_voxelize(verts, tris, grid: Grid, seed, rep_tri, ws, counters=None, stream=None) -> None:
+    _check(lib().rtsdf_voxelize(_dev(verts, torch.float32, "verts"), verts.shape[0],
+                                _dev(tris, torch.int32, "tris"), tris.shape[0], C.byref(grid),
+                                _dev(seed, torch.int32, "seed"), _dev(rep_tri, torch.int32, "rep_tri"),
+                                _dev(ws, torch.uint8, "ws"), ws.numel(),
+                                _dev(counters, torch.int32, "counters"), _stream(stream)), "rtsdf_voxelize")
+
+
+def rtsdf_build_bvh(verts, tris, grid: Grid, bvh, ws, counters=None, stream=None) -> None:
+    _check(lib().rtsdf_build_bvh(_dev(verts, torch.float32, "verts"), verts.shape[0],
+                                 _dev(tris, torch.int32, "tris"), tris.shape[0], C.byref(grid),
+                                 _dev(bvh, torch.uint8, "bvh"), bvh.numel(), _dev(ws, torch.uint8, "ws"), ws.numel(),
+                                 _dev(counters, torch.int32, "counters"), _stream(stream)), "rtsdf_build_bvh")
+
+
+def rtsdf_jfa(grid: Grid, buf_a, buf_b, steps, stream=None):
+    """Runs the passes; returns the tensor (buf_a or buf_b) that holds the result."""
+    arr = (C.c_int32 * max(1, len(steps)))(*[int(k) for k in steps])
+    res = C.c_void_p()
+    _check(lib().rtsdf_jfa(C.byref(grid), _dev(buf_a, torch.int32, "buf_a"), _dev(buf_b, torch.int32, "buf_b"),
+                           arr, len(steps), C.byref(res), _stream(stream)), "rtsdf_jfa")
+    return buf_a if res.value == buf_a.data_ptr() else buf_b
+
+
+def rtsdf_refine(grid: Grid, verts, tris, bvh, nearest, rep_tri, params: RefineParams, dist_bits, front, back,
+                 sdf_out, ws, counters=None, stream=None) -> None:
+    _check(lib().rtsdf_refine(C.byref(grid), _dev(verts, torch.float32, "verts"), verts.shape[0],
+                              _dev(tris, torch.int32, "tris"), tris.shape[0], _dev(bvh, torch.uint8, "bvh"),
+                              bvh.numel(), _dev(nearest, torch.int32, "nearest"),
+                              _dev(rep_tri, torch.int32, "rep_tri"), C.byref(params),
+                              _dev(dist_bits, torch.int32, "dist_bits"), _dev(front, torch.int32, "front"),
+                              _dev(back, torch.int32, "back"), _dev(sdf_out, torch.float32, "sdf_out"),
+                              _dev(ws, torch.uint8, "ws"), ws.numel(), _dev(counters, torch.int32, "counters"),
+                              _stream(stream)), "rtsdf_refine")
+
+
+def rtsdf_shadow(grid: Grid, sdf, pos, nrm, params: ShadowParams, vis, stream=None) -> None:
+    _check(lib().rtsdf_shadow(C.byref(grid), _dev(sdf, torch.float32, "sdf"), _dev(pos, torch.float32, "pos"),
+                              _dev(nrm, torch.float32, "nrm"), pos.shape[0], C.byref(params),
+                              _dev(vis, torch.float32, "vis"), _stream(stream)), "rtsdf_shadow")
+
+
+def rtsdf_kernel_launches() -> int:
+    return int(lib().rtsdf_kernel_launches())
+
+
+def counters_dict(counters: torch.Tensor) -> dict:
+    vals = counters.cpu().tolist()
+    return {f: int(v) & 0xFFFFFFFF for f, v in zip(COUNTER_FIELDS, vals)}
+
+
+# ------------------------------------------------------------ a frame pipeline
+
+class Pipeline:
+    """Owns the device buffers of one scene size and runs the hot path through the
+    C-ABI: voxelize -> BVH -> jump flood -> refine (one frame) -> shadow.
+
+    uint32 state (dist_bits, front, back) is held in int32 tensors of the same bits.
+    """
+
+    def __init__(self, grid, n_verts: int, n_tris: int, device="cuda"):
+        self.g = make_grid(grid)
+        self.T, self.V = int(n_tris), int(n_verts)
+        dev = torch.device(device)
+        shp = (grid.nz, grid.ny, grid.nx)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.buf_a = torch.empty(shp, **i32)
+        self.buf_b = torch.empty(shp, **i32)
+        self.rep_tri = torch.empty(shp, **i32)
+        self.dist_bits = torch.zeros(shp, **i32)
+        self.front = torch.zeros(shp, **i32)
+        self.back = torch.zeros(shp, **i32)
+        self.sdf = torch.empty(shp, dtype=torch.float32, device=dev)
+        self.counters = torch.zeros(8, **i32)
+        u8 = dict(dtype=torch.uint8, device=dev)
+        self.ws_vox = torch.empty(rtsdf_voxelize_workspace(self.T, self.g), **u8)
+        self.bvh = torch.empty(rtsdf_bvh_bytes(self.T), **u8)
+        self.ws_bvh = torch.empty(rtsdf_bvh_workspace(self.T), **u8)
+        self.ws_refine = torch.empty(rtsdf_refine_workspace(self.g), **u8)
+        self.nearest = None
+
+    def voxelize(self, verts, tris, stream=None):
+        rtsdf_voxelize(verts, tris, self.g, self.buf_a, self.rep_tri, self.ws_vox, self.counters, stream)
+        return self.buf_a
+
+    def build_bvh(self, verts, tris, stream=None):
+        rtsdf_build_bvh(verts, tris, self.g, self.bvh, self.ws_bvh, self.counters, stream)
+
+    def jfa(self, steps, stream=None):
+        self.nearest = rtsdf_jfa(self.g, self.buf_a, self.buf_b, steps, stream)
+        return self.nearest
+
+    def refine(self, verts, tris, params: RefineParams, stream=None):
+        rtsdf_refine(self.g, verts, tris, self.bvh, self.nearest, self.rep_tri, params, self.dist_bits, self.front,
+                     self.back, self.sdf, self.ws_refine, self.counters, stream)
+        return self.sdf
+
+    def rebuild(self, verts, tris, steps, params: RefineParams, stream=None):
+        self.voxelize(verts, tris, stream)
+        self.build_bvh(verts, tris, stream)
+        self.jfa(steps, stream)
+        return self.refine(verts, tris, params, stream)
+
+    def shadow(self, pos, nrm, params: ShadowParams, vis=None, stream=None):
+        if vis is None:
+            vis = torch.empty(pos.shape[0], dtype=torch.float32, device=pos.device)
+        rtsdf_shadow(self.g, self.sdf, pos, nrm, params, vis, stream)
+        return vis

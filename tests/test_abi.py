@@ -1,0 +1,119 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point that
+include/rtsdf.h declares, and rejects bad arguments before touching any memory
+(fake device addresses are never dereferenced on these paths)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2210_06160_gb300 import build, rtsdf
+    build.build()
+    return rtsdf.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "rtsdf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rtsdf_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_status_strings(lib):
+    assert lib.rtsdf_version() >= 100
+    assert lib.rtsdf_status_string(0) == b"ok"
+    assert b"invalid" in lib.rtsdf_status_string(1)
+
+
+FAKE = 0x7F0000000000  # 256-byte aligned, never dereferenced
+
+
+def _grid(nx=8, ny=8, nz=8, h=0.1):
+    from paper_2210_06160_gb300.rtsdf import Grid
+    return Grid(nx, ny, nz, (C.c_float * 3)(0, 0, 0), h)
+
+
+def test_grid_validation(lib):
+    from paper_2210_06160_gb300.rtsdf import Grid
+    bad = [_grid(0, 8, 8), _grid(8, 1024, 8), _grid(8, 8, 8, 0.0), _grid(8, 8, 8, float("nan")),
+           Grid(8, 8, 8, (C.c_float * 3)(0, float("inf"), 0), 0.1)]
+    for g in bad:
+        assert lib.rtsdf_voxelize_workspace(10, C.byref(g)) == 0
+        assert lib.rtsdf_voxelize(C.c_void_p(FAKE), 3, C.c_void_p(FAKE), 1, C.byref(g), C.c_void_p(FAKE),
+                                  C.c_void_p(FAKE), C.c_void_p(FAKE), 1 << 40, None, None) == 1
+    g = _grid()
+    assert lib.rtsdf_voxelize_workspace(10, C.byref(g)) > 8 * 512
+
+
+def test_pointer_and_size_validation(lib):
+    g = _grid()
+    ws = lib.rtsdf_voxelize_workspace(4, C.byref(g))
+    P = C.c_void_p
+    # misaligned grid buffer
+    assert lib.rtsdf_voxelize(P(FAKE), 3, P(FAKE), 1, C.byref(g), P(FAKE + 4), P(FAKE), P(FAKE), ws, None, None) == 1
+    # null triangles with T > 0
+    assert lib.rtsdf_voxelize(P(FAKE), 3, None, 1, C.byref(g), P(FAKE), P(FAKE), P(FAKE), ws, None, None) == 1
+    # negative counts
+    assert lib.rtsdf_voxelize(P(FAKE), -1, P(FAKE), 1, C.byref(g), P(FAKE), P(FAKE), P(FAKE), ws, None, None) == 1
+    # workspace too small
+    assert lib.rtsdf_voxelize(P(FAKE), 3, P(FAKE), 4, C.byref(g), P(FAKE), P(FAKE), P(FAKE), ws - 1, None,
+                              None) == 2
+    T = 100
+    assert lib.rtsdf_build_bvh(P(FAKE), 3, P(FAKE), T, C.byref(g), P(FAKE), lib.rtsdf_bvh_bytes(T) - 1, P(FAKE),
+                               lib.rtsdf_bvh_workspace(T), None, None) == 2
+
+
+def test_jfa_validation(lib):
+    g = _grid()
+    P = C.c_void_p
+    res = C.c_void_p()
+    steps = (C.c_int32 * 2)(4, 0)
+    assert lib.rtsdf_jfa(C.byref(g), P(FAKE), P(FAKE + 4096), steps, 2, C.byref(res), None) == 1  # step 0
+    steps = (C.c_int32 * 1)(4)
+    assert lib.rtsdf_jfa(C.byref(g), P(FAKE), P(FAKE), steps, 1, C.byref(res), None) == 1  # aliased buffers
+    assert lib.rtsdf_jfa(C.byref(g), P(FAKE), P(FAKE + 4096), steps, -1, C.byref(res), None) == 1
+    # zero passes: nothing enqueued, result is buf_a
+    assert lib.rtsdf_jfa(C.byref(g), P(FAKE), P(FAKE + 4096), steps, 0, C.byref(res), None) == 0
+    assert res.value == FAKE
+
+
+def test_refine_and_shadow_parameter_validation(lib):
+    from paper_2210_06160_gb300.rtsdf import RefineParams, ShadowParams
+    g = _grid()
+    P = C.c_void_p
+    ws = lib.rtsdf_refine_workspace(C.byref(g))
+    bvh = lib.rtsdf_bvh_bytes(1)
+    for rp in (RefineParams(3.0, 0, 8.0, 1.0), RefineParams(-1.0, 8, 8.0, 1.0), RefineParams(3.0, 8, 0.0, 1.0)):
+        assert lib.rtsdf_refine(C.byref(g), P(FAKE), 3, P(FAKE), 1, P(FAKE), bvh, P(FAKE), P(FAKE), C.byref(rp),
+                                P(FAKE), P(FAKE), P(FAKE), P(FAKE), P(FAKE), ws, None, None) == 1
+    rp = RefineParams(3.0, 8, 8.0, 1.0)
+    assert lib.rtsdf_refine(C.byref(g), P(FAKE), 3, P(FAKE), 1, P(FAKE), bvh, P(FAKE), P(FAKE), C.byref(rp),
+                            P(FAKE), P(FAKE), P(FAKE), P(FAKE), P(FAKE), ws - 1, None, None) == 2
+    sp = ShadowParams((C.c_float * 3)(0, 0, 0), 8.0, 10, 1.0)
+    assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
+    sp = ShadowParams((C.c_float * 3)(0, 1, 0), 8.0, 10, 0.0)
+    assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The binding raises when the compiled library is absent instead of computing
+    anything itself, and nothing in the package imports the oracle."""
+    import paper_2210_06160_gb300 as pkg
+    pkg_dir = os.path.dirname(pkg.__file__)
+    for fn in os.listdir(pkg_dir):
+        if fn.endswith(".py"):
+            src = open(os.path.join(pkg_dir, fn)).read()
+            assert "import oracle" not in src and "from oracle" not in src, fn
+    src = open(os.path.join(pkg_dir, "rtsdf.py")).read()
+    assert "raise RtsdfError" in src

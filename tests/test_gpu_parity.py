@@ -1,0 +1,166 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Bars: seeds, representative triangles, flooded seeds, hit counts and front/back
+votes bit-exact; refined distances bit-exact (both sides take the same FP32
+operations); signed field within 1e-5 voxel; shadow visibility within 1e-4.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2210_06160_gb300 import rtsdf as rt
+from paper_2210_06160_gb300 import scenes
+from tests.gpu_helpers import compare_rebuild, gpu_rebuild, gpu_shadow, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SHADOW_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def test_tiny_icosphere_full_parity():
+    sc = scenes.scene_tiny(shadow_res=128)
+    ref = oracle.rebuild(sc)
+    got, P = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    assert got["counters"]["masked_voxels"] == int(ref["mask"].sum())
+    assert got["counters"]["rays_failed"] == 0 and got["counters"]["stack_overflow"] == 0
+    vis_ref = oracle.shadow(sc.grid, ref["sdf"], sc.recv_pos, sc.recv_nrm, sc.shadow)
+    vis = P.shadow(to_dev(sc.recv_pos), to_dev(sc.recv_nrm), rt.make_shadow_params(sc.shadow)).cpu().numpy()
+    assert np.abs(vis - vis_ref).max() <= SHADOW_TOL
+
+
+def test_small_room_accumulated_frames_parity():
+    sc = scenes.scene_small_room()
+    ref = oracle.rebuild(sc)
+    got, P = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    vis_ref = oracle.shadow(sc.grid, ref["sdf"], sc.recv_pos, sc.recv_nrm, sc.shadow)
+    vis = P.shadow(to_dev(sc.recv_pos), to_dev(sc.recv_nrm), rt.make_shadow_params(sc.shadow)).cpu().numpy()
+    assert np.abs(vis - vis_ref).max() <= SHADOW_TOL
+
+
+def _random_scene(seed=0, dims=(37, 21, 29), n=60, R=5):
+    rng = np.random.default_rng(seed)
+    g = scenes.Grid(*dims, (-0.3, 0.1, -0.2), 0.05)
+    ext = np.array(dims) * g.h
+    c = np.array(g.origin) + rng.uniform(-0.1, 1.1, (n, 3)) * ext  # some outside the grid
+    tri = c[:, None, :] + rng.normal(0, 0.15, (n, 3, 3)) * rng.choice([0.1, 1.0, 3.0], (n, 1, 1))
+    V = tri.reshape(-1, 3).astype(np.float32)
+    T = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    T[5] = [0, 0, 0]            # degenerate (a point)
+    T[6] = [1, 2, 2]            # degenerate (a segment)
+    T[7] = [0, 1, 10_000]       # invalid index: skipped
+    V[3 * 9] = np.nan           # non-finite vertex: triangle 9 skipped
+    rp = scenes.RefineParams(mask_vox=2.5, rays_per_voxel=R, max_ray_vox=6.0, beta_vox=0.5, key=(11, 22))
+    return scenes.Scene("random", V, T, g, rp, scenes.ShadowParams(steps=40, max_step_vox=2.0),
+                        scenes.jfa_steps(g), 1, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+
+
+@pytest.mark.parametrize("R", [5, 16])
+def test_random_triangles_ragged_grid_parity(R):
+    """Ragged dims, triangles partly outside, degenerate and invalid triangles, and
+    a ray count that does not divide the warp (atomic merge path)."""
+    sc = _random_scene(R=R)
+    ref = oracle.rebuild(sc)
+    got, _ = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    assert got["counters"]["skipped_triangles"] == 2 * 2  # voxelize + BVH each count both
+
+
+def test_jfa_random_seeds_and_shapes_parity():
+    rng = np.random.default_rng(1)
+    for dims in [(1, 1, 1), (2, 3, 1), (33, 17, 65), (1023, 2, 3), (64, 64, 64)]:
+        g = scenes.Grid(*dims, (0.0, 0.0, 0.0), 1.0)
+        nvox = g.nvox
+        seeds = np.full(g.shape_zyx, -1, np.int32)
+        for frac in (0.0, 0.001, 0.05):
+            cnt = int(nvox * frac)
+            flat = rng.choice(nvox, cnt, replace=False) if cnt else np.zeros(0, int)
+            k, j, i = np.unravel_index(flat, g.shape_zyx)
+            s = seeds.copy()
+            s[k, j, i] = (k << 20) | (j << 10) | i
+            steps = scenes.jfa_steps(g, extra_one=True) + [3, 7]
+            want = oracle.jfa(g, s, steps)
+            a, b = to_dev(s), torch.empty_like(to_dev(s))
+            out = rt.rtsdf_jfa(rt.make_grid(g), a, b, steps)
+            np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_empty_mesh_gives_empty_field_and_full_light():
+    g = scenes.Grid(16, 12, 10, (0.0, 0.0, 0.0), 0.1)
+    sc = scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), g,
+                      scenes.RefineParams(rays_per_voxel=4), scenes.ShadowParams(steps=20, max_step_vox=2.0),
+                      scenes.jfa_steps(g), 1, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+    ref = oracle.rebuild(sc)
+    got, P = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    assert np.all(got["nearest"] == -1)
+    assert np.all(got["sdf"] == np.float32(16 + 12 + 10) - np.float32(1.0))
+    pos, nrm = scenes.receivers_plane(0.1, 0.0, 1.6, 0.0, 1.0, 8, 8)
+    vis = P.shadow(to_dev(pos), to_dev(nrm), rt.make_shadow_params(sc.shadow)).cpu().numpy()
+    assert np.all(vis == 1.0)
+
+
+def test_single_triangle_and_bvh_of_one_leaf():
+    g = scenes.Grid(20, 20, 20, (0.0, 0.0, 0.0), 0.05)
+    V = np.array([[0.2, 0.5, 0.2], [0.8, 0.5, 0.3], [0.4, 0.5, 0.9]], np.float32)
+    T = np.array([[0, 2, 1]], np.int32)
+    sc = scenes.Scene("one", V, T, g, scenes.RefineParams(mask_vox=3.0, rays_per_voxel=8, key=(5, 6)),
+                      scenes.ShadowParams(steps=30, max_step_vox=1.0), scenes.jfa_steps(g), 1,
+                      np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+    ref = oracle.rebuild(sc)
+    got, _ = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    assert got["counters"]["rays_hit"] > 0
+
+
+def test_results_are_deterministic():
+    sc = scenes.scene_small_room(seed=3, n=40)
+    a, _ = gpu_rebuild(sc)
+    for _ in range(2):
+        b, _ = gpu_rebuild(sc)
+        for k in ("seed", "rep_tri", "nearest", "dist_bits", "front", "back"):
+            np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a["sdf"].view(np.uint32), b["sdf"].view(np.uint32))
+
+
+def test_shadow_parity_on_analytic_field():
+    """Shadow kernel alone on a seeded analytic field (sphere + floor), ragged grid,
+    bias and hit epsilon set, receivers with tilted normals."""
+    g = scenes.Grid(50, 40, 30, (0.0, 0.0, 0.0), 0.04)
+    k, j, i = np.meshgrid(*(np.arange(n) + 0.5 for n in (30, 40, 50)), indexing="ij")
+    f = np.minimum(np.sqrt((i - 25) ** 2 + (j - 25) ** 2 + (k - 15) ** 2) - 7.0, j - 3.0).astype(np.float32)
+    rng = np.random.default_rng(4)
+    pos = np.stack([rng.uniform(0, 2.0, 5000), np.full(5000, 0.13), rng.uniform(0, 1.2, 5000)], 1).astype(np.float32)
+    nrm = rng.normal(0, 0.2, (5000, 3)) + [0, 1, 0]
+    nrm = (nrm / np.linalg.norm(nrm, axis=1, keepdims=True)).astype(np.float32)
+    for sp in (scenes.ShadowParams(light_dir=(0.3, 1.0, 0.2), k=8.0, steps=96, max_step_vox=1.25),
+               scenes.ShadowParams(light_dir=(-0.5, 0.7, 0.1), k=3.0, steps=64, max_step_vox=4.0,
+                                   bias_vox=0.25, hit_eps_vox=0.05, start_offset_vox=0.5)):
+        want = oracle.shadow(g, f, pos, nrm, sp)
+        got = gpu_shadow(g, f, pos, nrm, sp)
+        assert np.abs(got - want).max() <= SHADOW_TOL
+
+
+def test_accumulation_is_monotone_and_resumable():
+    """Frames 0..3 in one run equal frames 0..1 then 2..3 resumed from the saved
+    state (counter-based directions make the state a complete checkpoint)."""
+    sc = scenes.scene_small_room(seed=5, n=40)
+    full, P = gpu_rebuild(sc, frames=4)
+    verts, tris = to_dev(sc.verts), to_dev(sc.tris)
+    part, P2 = gpu_rebuild(sc, frames=2)
+    for f in (2, 3):
+        rp = dataclasses.replace(sc.refine, frame_index=f, accumulate=True)
+        P2.refine(verts, tris, rt.make_refine_params(rp))
+    for k in ("dist_bits", "front", "back"):
+        np.testing.assert_array_equal(getattr(P2, k).cpu().numpy(), getattr(P, k).cpu().numpy())
+    m = full["front"] + full["back"] >= part["front"] + part["back"]
+    assert np.all(m)
