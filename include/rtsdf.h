@@ -129,6 +129,31 @@ rtsdf_status rtsdf_build_bvh(const float* verts, int32_t V, const int32_t* tris,
                              const rtsdf_grid* g, void* bvh, size_t bvh_bytes,
                              void* ws, size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream);
 
+/* ---------------------------------------------------------------- BVH, no allocation */
+
+/* Largest mesh rtsdf_build_bvh_noalloc accepts, and the device memory its fixed
+ * scratch array occupies on every GPU that loads this library, until exit. */
+#define RTSDF_NOALLOC_MAX_TRIS 131072
+#define RTSDF_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* No counterpart in the paper: a convenience of this library.  rtsdf_build_bvh
+ * without a caller workspace, for hosts that cannot allocate device memory on the
+ * library's behalf, e.g. an engine whose memory manager owns the GPU and forbids
+ * cudaMalloc inside its frame loop (cudaMalloc can synchronise the device and stall
+ * the frame).  Its scratch is one fixed array in device memory inside the library;
+ * the call itself allocates nothing.  The caller still passes the mesh and the
+ * output BVH buffer; arguments, outputs and errors are those of rtsdf_build_bvh, and
+ * T > RTSDF_NOALLOC_MAX_TRIS returns RTSDF_ENOMEM.
+ * The first call on a device looks up the array's device address (one-time set-up
+ * per device, with that device current); make that first call before any stream
+ * capture.  Every call on a device uses the same array, which keeps the previous
+ * call's contents (the build clears what must start at zero): calls that can
+ * overlap on the GPU (other streams, other host threads) race, so the caller must
+ * serialise them. */
+rtsdf_status rtsdf_build_bvh_noalloc(const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                                     const rtsdf_grid* g, void* bvh, size_t bvh_bytes,
+                                     rtsdf_counters* counters, rtsdf_stream stream);
+
 /* ---------------------------------------------------------------- jump flooding */
 
 /* Sec. 2.2 (Jump Flooding, after Rong & Tan 2006, extended to 3D): for each

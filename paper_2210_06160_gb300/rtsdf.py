@@ -64,6 +64,7 @@ _SIGS = {
     "rtsdf_bvh_workspace": (C.c_size_t, [C.c_int32]),
     "rtsdf_build_bvh": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.POINTER(Grid), _P, C.c_size_t, _P, C.c_size_t,
                                   _P, _P]),
+    "rtsdf_build_bvh_noalloc": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.POINTER(Grid), _P, C.c_size_t, _P, _P]),
     "rtsdf_jfa": (C.c_int, [C.POINTER(Grid), _P, _P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_void_p), _P]),
     "rtsdf_refine_workspace": (C.c_size_t, [C.POINTER(Grid)]),
     "rtsdf_refine": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t, _P, _P,
@@ -161,6 +162,16 @@ def rtsdf_build_bvh(verts, tris, grid: Grid, bvh, ws, counters=None, stream=None
                                  _dev(tris, torch.int32, "tris"), tris.shape[0], C.byref(grid),
                                  _dev(bvh, torch.uint8, "bvh"), bvh.numel(), _dev(ws, torch.uint8, "ws"), ws.numel(),
                                  _dev(counters, torch.int32, "counters"), _stream(stream)), "rtsdf_build_bvh")
+
+
+def rtsdf_build_bvh_noalloc(verts, tris, grid: Grid, bvh, counters=None, stream=None) -> None:
+    """rtsdf_build_bvh with the library's fixed internal scratch (no workspace);
+    at most RTSDF_NOALLOC_MAX_TRIS triangles; overlapping calls race."""
+    _check(lib().rtsdf_build_bvh_noalloc(_dev(verts, torch.float32, "verts"), verts.shape[0],
+                                         _dev(tris, torch.int32, "tris"), tris.shape[0], C.byref(grid),
+                                         _dev(bvh, torch.uint8, "bvh"), bvh.numel(),
+                                         _dev(counters, torch.int32, "counters"), _stream(stream)),
+           "rtsdf_build_bvh_noalloc")
 
 
 def rtsdf_jfa(grid: Grid, buf_a, buf_b, steps, stream=None):
