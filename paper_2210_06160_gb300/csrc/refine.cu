@@ -1,16 +1,22 @@
 // Coarse field, ray mask and ray-sampled refinement (Sec. 2.1-2.3).
 //
-//  k_resolve:  one thread per voxel.  Coarse distance u_c to the representative
-//              triangle of the flooded seed; unmasked voxels get their final
-//              value (u_c - beta); masked voxels initialise their refine state
-//              and are appended to a compacted list (warp ballot + one atomic
-//              per warp).
-//  k_trace:    persistent; warps take 32 (voxel, ray) items at a time from a
-//              global counter.  Each lane draws its Philox direction and walks
-//              the BVH (stack traversal, nearest child first, boxes clipped to
-//              the closest hit so far); per voxel, the closest hits are reduced
-//              in-warp when R divides 32, else merged with atomics.
-//  k_finalize: signs the masked voxels from their front/back votes.
+//  k_resolve: one thread per voxel, blocks of 32x4x4 voxels = 8 bricks of 4^3.
+//             Coarse distance u_c to the representative triangle of the flooded
+//             seed; unmasked voxels get their final value (u_c - beta); masked
+//             voxels initialise their refine state.  Per brick a 64-bit mask of
+//             its masked voxels is assembled from warp ballots, and bricks with
+//             any masked voxel are appended to a work list.
+//  k_refine:  persistent warp-per-voxel-batch refinement, one 4^3 brick per
+//             64-thread CTA.  Warp 0 walks the BVH once for the whole brick with
+//             the box every ray of the brick stays inside (voxel centres grown
+//             by the ray length) and stages the overlapping triangles in shared
+//             memory; every thread owns one masked voxel and tests its rays
+//             against the staged triangles after a bounding-sphere cull of the
+//             (voxel, triangle) pair.  The closest hit of each ray (ties to the
+//             lower triangle id) lowers the voxel's distance and adds one
+//             front/back vote; the thread then writes the accumulated state and
+//             the signed value.  Staging runs in rounds when a brick has more
+//             candidates than the buffer holds.
 #include <float.h>
 
 #include "rtsdf_device.cuh"
@@ -18,21 +24,38 @@
 
 namespace rtsdf {
 
+constexpr int kB = 4;                // brick edge (voxels)
+constexpr int kRefineThreads = 64;   // independent warps, one brick each
+constexpr int kCandCapW = 64;        // staged triangles per warp and round
+constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
+constexpr int kRaysPerLane = 8;      // rays of a voxel per group (one lane per voxel)
+constexpr int kQueueCap = 32 + 256;  // queued ray/triangle items per warp
+
 struct RefineWs {
-    int32_t* list;
-    uint32_t* count;    // [0] masked voxels, [1] work counter
+    uint32_t* count;            // [0] active bricks, [1] work counter, [2] walks that overflowed
+    unsigned long long* bmask;  // per brick: bit (lz*16 + ly*4 + lx) set for masked voxels
+    int32_t* blist;             // active bricks
 };
 
+static size_t nbricks(const rtsdf_grid& g) {
+    return (size_t)((g.nx + kB - 1) / kB) * ((g.ny + kB - 1) / kB) * ((g.nz + kB - 1) / kB);
+}
+
 static size_t refine_ws_layout(const rtsdf_grid& g, char* base, RefineWs* w) {
-    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    const size_t nb = nbricks(g);
     size_t off = 0;
-    char* c = base;
-    off += 256;
-    char* l = base ? base + off : nullptr;
-    off += align_up(4 * nvox, 256);
+    auto take = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off += align_up(bytes, 256);
+        return p;
+    };
+    char* c = take(64);
+    char* m = take(8 * nb);
+    char* l = take(4 * nb);
     if (w) {
         w->count = reinterpret_cast<uint32_t*>(c);
-        w->list = reinterpret_cast<int32_t*>(l);
+        w->bmask = reinterpret_cast<unsigned long long*>(m);
+        w->blist = reinterpret_cast<int32_t*>(l);
     }
     return off;
 }
@@ -51,20 +74,25 @@ struct RefineArgs {
     float tmax;
     uint32_t k0, k1, frame, scene;
     int accumulate, fallback;
+    int nbx, nby, nbz;
 };
 
-__global__ void __launch_bounds__(256) k_resolve(RefineArgs a, const int32_t* __restrict__ nearest,
-                                                 const int32_t* __restrict__ rep_tri, uint32_t* __restrict__ dist_bits,
-                                                 uint32_t* __restrict__ front, uint32_t* __restrict__ back,
-                                                 float* __restrict__ sdf, int32_t* __restrict__ list,
-                                                 uint32_t* __restrict__ count) {
-    const int64_t nvox = (int64_t)a.g.nx * a.g.ny * a.g.nz;
-    const int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// ------------------------------------------------------------------ resolve
+
+__global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __restrict__ nearest,
+                                                 const int32_t* __restrict__ rep_tri,
+                                                 uint32_t* __restrict__ dist_bits, uint32_t* __restrict__ front,
+                                                 uint32_t* __restrict__ back, float* __restrict__ sdf,
+                                                 unsigned long long* __restrict__ bmask,
+                                                 int32_t* __restrict__ blist, uint32_t* __restrict__ count) {
+    __shared__ unsigned long long smask[8];
+    const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz = threadIdx.x >> 7;
+    const int i = blockIdx.x * 32 + tx, j = blockIdx.y * kB + ty, k = blockIdx.z * kB + tz;
+    if (threadIdx.x < 8) smask[threadIdx.x] = 0ull;
+    __syncthreads();
     bool masked = false;
-    if (lin < nvox) {
-        const int64_t plane = (int64_t)a.g.nx * a.g.ny;
-        const int k = (int)(lin / plane), rem = (int)(lin - (int64_t)k * plane);
-        const int j = rem / a.g.nx, i = rem - j * a.g.nx;
+    if (i < a.g.nx && j < a.g.ny && k < a.g.nz) {
+        const int64_t lin = ((int64_t)k * a.g.ny + j) * a.g.nx + i;
         const int32_t s = __ldg(nearest + lin);
         int32_t rep = -1;
         int si = 0, sj = 0, sk = 0;
@@ -96,176 +124,351 @@ __global__ void __launch_bounds__(256) k_resolve(RefineArgs a, const int32_t* __
         }
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, masked);
-    if (bal == 0u) return;
-    const uint32_t lane = lane_id();
-    uint32_t base = 0;
-    if (lane == (uint32_t)(__ffs(bal) - 1)) base = atomicAdd(count, (uint32_t)__popc(bal));
-    base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-    if (masked) list[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)lin;
+    if (tx == 0 && bal) {
+        const int shift = (tz * kB + ty) * kB;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned long long nib = (bal >> (4 * b)) & 0xFu;
+            if (nib) atomicOr(&smask[b], nib << shift);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int bx = blockIdx.x * 8 + threadIdx.x;
+        const bool valid = threadIdx.x < 8 && bx < a.nbx;
+        const unsigned long long m = valid ? smask[threadIdx.x] : 0ull;
+        const int64_t b = ((int64_t)blockIdx.z * a.nby + blockIdx.y) * a.nbx + bx;
+        if (valid) bmask[b] = m;
+        const uint32_t act = __ballot_sync(0xffffffffu, m != 0ull);
+        uint32_t base = 0;
+        if (threadIdx.x == 0 && act) base = atomicAdd(count, (uint32_t)__popc(act));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (m) blist[base + __popc(act & ((1u << threadIdx.x) - 1u))] = (int32_t)b;
+    }
 }
 
-struct Hit {
-    float t;
-    int id;
-    bool front;
+// ------------------------------------------------------------------ refine
+
+__device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, float3 qlo, float3 qhi) {
+    return lo.x <= qhi.x && hi.x >= qlo.x && lo.y <= qhi.y && hi.y >= qlo.y && lo.z <= qhi.z && hi.z >= qlo.z;
+}
+
+struct Cand {
+    float4 v0;   // xyz, w = triangle id bits
+    float4 e1;
+    float4 e2;
+    float4 sph;  // centre xyz, w = (radius + ray length + margin)^2
 };
 
-__device__ __forceinline__ bool slab(float4 lo, float4 hi, float3 o, float3 inv, float tclip, float& tnear) {
-    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
-    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
-    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tclip));
-    tnear = tn;
-    return tn <= tf;
-}
-
-constexpr int kStack = 64;
-
-__device__ __forceinline__ void leaf_test(const BvhLeaf* __restrict__ leaves, int j, float3 o, float3 d, float tmax,
-                                          Hit& best, float& tclip) {
-    const float4 v0 = __ldg(&leaves[j].v0), e1 = __ldg(&leaves[j].e1), e2 = __ldg(&leaves[j].e2);
-    const int id = __float_as_int(v0.w);
-    float t;
-    bool f;
-    if (ray_tri(o, d, make_float3(v0.x, v0.y, v0.z), make_float3(e1.x, e1.y, e1.z), make_float3(e2.x, e2.y, e2.z),
-                tmax, t, f)) {
-        if (t < best.t || (t == best.t && id < best.id)) {
-            best.t = t;
-            best.id = id;
-            best.front = f;
-            tclip = t;
+// Warp-cooperative walk of the BVH for the query box: pops up to 32 nodes per
+// step from the warp's stack and stages the leaves it reaches; stops when the
+// stack is empty or the staging buffer could overflow on the next step.
+// Returns the new candidate count; *sp_io is the stack depth.
+__device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes, const BvhLeaf* __restrict__ leaves,
+                                              int n_inner, int n_leaves, float3 qlo, float3 qhi, int* stack,
+                                              int& sp, Cand* cand, int nc, float tmax, bool& overflow) {
+    const int lane = threadIdx.x & 31;
+    const int nc0 = nc;
+    int guard = 0;
+    while (sp > 0 && nc <= kCandCapW - 64) {
+        if (++guard > n_inner + 64) {  // a well-formed tree is exhausted long before
+            overflow = true;
+            sp = 0;
+            break;
         }
-    }
-}
-
-// Closest hit among all triangles with 0 < t <= tmax (ties -> lower id).
-// n_inner: number of inner nodes (n_leaves - 1, at least 1).  Every node is
-// entered at most once per ray in a well-formed tree; the loop is additionally
-// bounded and index-checked so that a malformed buffer ends the walk (flagged as
-// overflow) instead of reading out of bounds or spinning.
-__device__ __forceinline__ Hit trace_ray(const BvhNode* __restrict__ nodes, const BvhLeaf* __restrict__ leaves,
-                                         int n_inner, int n_leaves, float3 o, float3 d, float tmax, bool& overflow) {
-    Hit best{FLT_MAX, 0x7fffffff, false};
-    const float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-    int stack[kStack];
-    int sp = 0, cur = 0;
-    float tclip = tmax;
-    for (int guard = 0; guard <= n_inner; ++guard) {
-        if (cur < 0 || cur >= n_inner) { overflow = true; break; }
-        const BvhNode* nd = nodes + cur;
-        const float4 lo0 = __ldg(&nd->lo0), hi0 = __ldg(&nd->hi0), lo1 = __ldg(&nd->lo1), hi1 = __ldg(&nd->hi1);
-        const int c0 = __float_as_int(lo0.w), c1 = __float_as_int(hi0.w);
-        float tn0, tn1;
-        bool h0 = slab(lo0, hi0, o, inv, tclip, tn0);
-        bool h1 = slab(lo1, hi1, o, inv, tclip, tn1);
-        if (h0 && c0 < 0) { if (~c0 < n_leaves) leaf_test(leaves, ~c0, o, d, tmax, best, tclip); h0 = false; }
-        if (h1 && c1 < 0) { if (~c1 < n_leaves) leaf_test(leaves, ~c1, o, d, tmax, best, tclip); h1 = false; }
-        int next;
-        if (h0 && h1) {
-            const bool first0 = tn0 <= tn1;
-            if (sp < kStack) stack[sp++] = first0 ? c1 : c0; else overflow = true;
-            next = first0 ? c0 : c1;
-        } else if (h0) {
-            next = c0;
-        } else if (h1) {
-            next = c1;
+        const int take = min(sp, 32);
+        int node = -1;
+        if (lane < take) node = stack[sp - 1 - lane];
+        sp -= take;
+        bool h0 = false, h1 = false;
+        int c0 = 0, c1 = 0;
+        if (node >= 0 && node < n_inner) {
+            const BvhNode* nd = nodes + node;
+            const float4 lo0 = __ldg(&nd->lo0), hi0 = __ldg(&nd->hi0);
+            const float4 lo1 = __ldg(&nd->lo1), hi1 = __ldg(&nd->hi1);
+            c0 = __float_as_int(lo0.w);
+            c1 = __float_as_int(hi0.w);
+            h0 = box_overlap(lo0, hi0, qlo, qhi);
+            h1 = n_leaves > 1 && box_overlap(lo1, hi1, qlo, qhi);
+            if (c0 < 0 && ~c0 >= n_leaves) h0 = false;
+            if (c1 < 0 && ~c1 >= n_leaves) h1 = false;
+        }
+        const int np = (h0 && c0 >= 0) + (h1 && c1 >= 0);
+        const int nl = (h0 && c0 < 0) + (h1 && c1 < 0);
+        int pp = np, pl = nl;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, pp, off);
+            const int v = __shfl_up_sync(0xffffffffu, pl, off);
+            if (lane >= off) {
+                pp += u;
+                pl += v;
+            }
+        }
+        const int tot_p = __shfl_sync(0xffffffffu, pp, 31);
+        const int tot_l = __shfl_sync(0xffffffffu, pl, 31);
+        int wp = sp + pp - np;
+        if (h0 && c0 >= 0) { if (wp < kStackCapW) stack[wp] = c0; ++wp; }
+        if (h1 && c1 >= 0) { if (wp < kStackCapW) stack[wp] = c1; ++wp; }
+        int wl = nc + pl - nl;
+        if (h0 && c0 < 0) {
+            const BvhLeaf* L = leaves + ~c0;
+            cand[wl].v0 = __ldg(&L->v0); cand[wl].e1 = __ldg(&L->e1); cand[wl].e2 = __ldg(&L->e2);
+            ++wl;
+        }
+        if (h1 && c1 < 0) {
+            const BvhLeaf* L = leaves + ~c1;
+            cand[wl].v0 = __ldg(&L->v0); cand[wl].e1 = __ldg(&L->e1); cand[wl].e2 = __ldg(&L->e2);
+            ++wl;
+        }
+        if (sp + tot_p > kStackCapW) {
+            overflow = true;
+            sp = kStackCapW;
         } else {
-            if (sp == 0) break;
-            next = stack[--sp];
+            sp += tot_p;
         }
-        cur = next;
+        nc += tot_l;
+        __syncwarp();
     }
-    return best;
+    // bounding spheres of the newly staged triangles
+    for (int c = nc0 + lane; c < nc; c += 32) {
+        const float4 v0 = cand[c].v0, e1 = cand[c].e1, e2 = cand[c].e2;
+        const float3 cen = make_float3(v0.x + (e1.x + e2.x) * (1.0f / 3.0f), v0.y + (e1.y + e2.y) * (1.0f / 3.0f),
+                                       v0.z + (e1.z + e2.z) * (1.0f / 3.0f));
+        const float3 a0 = make_float3(v0.x - cen.x, v0.y - cen.y, v0.z - cen.z);
+        const float3 a1 = make_float3(a0.x + e1.x, a0.y + e1.y, a0.z + e1.z);
+        const float3 a2 = make_float3(a0.x + e2.x, a0.y + e2.y, a0.z + e2.z);
+        const float r = sqrtf(fmaxf(fmaxf(dot3(a0, a0), dot3(a1, a1)), dot3(a2, a2)));
+        const float lim = r + tmax + 0.01f + 1e-5f * (fabsf(cen.x) + fabsf(cen.y) + fabsf(cen.z) + r + tmax);
+        cand[c].sph = make_float4(cen.x, cen.y, cen.z, lim * lim);
+        cand[c].e1.w = lim - tmax;  // radius of the sphere any accepted hit point lies in
+    }
+    __syncwarp();
+    return nc;
 }
 
-__global__ void __launch_bounds__(256) k_trace(RefineArgs a, const BvhHeader* __restrict__ hdr,
-                                               const BvhNode* __restrict__ nodes, const BvhLeaf* __restrict__ leaves,
-                                               const int32_t* __restrict__ list, uint32_t* __restrict__ count,
-                                               uint32_t* __restrict__ dist_bits, uint32_t* __restrict__ front,
-                                               uint32_t* __restrict__ back, rtsdf_counters* counters) {
+// Per-warp shared state of k_refine.
+struct WarpSmem {
+    Cand cand[kCandCapW];
+    int stack[kStackCapW];
+    uint32_t queue[kQueueCap];      // (candidate << 8) | (slot << 3) | ray
+    float4 origin[32];              // voxel centres of the pass's slots
+    float4 dir[8][32];              // ray directions of the group, [ray][slot]
+    unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
+};
+
+// Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
+// closest hit per ray (ties to the lower id) is kept with a 64-bit atomicMin.
+__device__ __forceinline__ void run_item(WarpSmem& w, uint32_t item, float tmax) {
+    const int c = (int)(item >> 8), slot = (int)((item >> 3) & 31u), r = (int)(item & 7u);
+    const float4 of = w.origin[slot], df = w.dir[r][slot];
+    const float3 o = make_float3(of.x, of.y, of.z), d = make_float3(df.x, df.y, df.z);
+    const float4 v0 = w.cand[c].v0, e1f = w.cand[c].e1, e2f = w.cand[c].e2;
+    const float3 A = make_float3(v0.x, v0.y, v0.z);
+    const float3 e1 = make_float3(e1f.x, e1f.y, e1f.z), e2 = make_float3(e2f.x, e2f.y, e2f.z);
+    float t;
+    bool front;
+    if (ray_tri(o, d, A, e1, e2, tmax, t, front)) {
+        const uint32_t id = (uint32_t)__float_as_int(v0.w);
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)((id << 1) | (front ? 1u : 0u));
+        atomicMin(&w.key[r][slot], key);
+    }
+}
+
+// One warp per brick; lane l owns voxel slot (pass*32 + l) and up to 8 rays of it
+// per group.  For every staged triangle the lane culls the (voxel, triangle) pair
+// by the triangle's bounding sphere grown by the ray length, then each ray by the
+// distance of the sphere's centre to the ray's line (and the side it lies on).
+// Surviving (voxel, ray, triangle) items are queued in shared memory and run
+// through the exact ray/triangle test 32 at a time, so the expensive test does
+// not diverge.  Both filters are conservative (their margins exceed FP32 rounding
+// of the exact test), so they never drop a triangle the exact test accepts; they
+// may use fused multiply-adds because they decide nothing the oracle decides.
+__global__ void __launch_bounds__(kRefineThreads, 12) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
+                                                              const BvhNode* __restrict__ nodes,
+                                                              const BvhLeaf* __restrict__ leaves,
+                                                              const int32_t* __restrict__ nearest,
+                                                              const int32_t* __restrict__ rep_tri,
+                                                              const unsigned long long* __restrict__ bmask,
+                                                              const int32_t* __restrict__ blist,
+                                                              uint32_t* __restrict__ count,
+                                                              uint32_t* __restrict__ dist_bits,
+                                                              uint32_t* __restrict__ front,
+                                                              uint32_t* __restrict__ back, float* __restrict__ sdf,
+                                                              rtsdf_counters* counters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
     const int n_leaves = hdr->n_leaves;
-    const uint64_t total = (uint64_t)count[0] * (uint64_t)a.R;
-    const uint32_t lane = lane_id();
-    const bool grouped = (32 % a.R) == 0;  // a voxel's R rays sit in one warp chunk
+    const int n_inner = n_leaves > 1 ? n_leaves - 1 : 1;
+    const uint32_t nact = count[0];
     uint32_t n_hit = 0, n_fail = 0, n_ovf = 0;
+    const float ext = a.tmax * 1.00001f + 1e-3f;
+
     while (true) {
-        uint64_t base = 0;
-        if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(count + 2), 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= total) break;
-        const uint64_t item = base + lane;
-        const bool active = item < total;
-        Hit h{FLT_MAX, 0x7fffffff, false};
-        int lin = 0;
-        if (active) {
-            const uint32_t li = (uint32_t)(item / (uint32_t)a.R), r = (uint32_t)(item % (uint32_t)a.R);
-            lin = __ldg(list + li);
-            const int64_t plane = (int64_t)a.g.nx * a.g.ny;
-            const int k = (int)(lin / plane), rem = (int)(lin - (int64_t)k * plane);
-            const int j = rem / a.g.nx, i = rem - j * a.g.nx;
-            const float3 o = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
-            float3 d;
-            if (!sphere_dir((uint32_t)lin, a.frame * (uint32_t)a.R + r, a.scene, a.k0, a.k1, d)) {
-                ++n_fail;
-            } else if (n_leaves > 0) {
-                bool ovf = false;
-                h = trace_ray(nodes, leaves, n_leaves > 1 ? n_leaves - 1 : 1, n_leaves, o, d, a.tmax, ovf);
-                n_ovf += ovf;
+        uint32_t wk = 0;
+        if (lane == 0) wk = atomicAdd(count + 1, 1u);
+        wk = __shfl_sync(0xffffffffu, wk, 0);
+        if (wk >= nact) break;
+        const int b = blist[wk];
+        const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
+        const unsigned long long m = bmask[b];
+        const int nm = __popcll(m);
+        // every ray of the brick stays inside its voxel centres' box grown by the ray length
+        const float3 qlo = make_float3((float)(bx * kB) + 0.5f - ext, (float)(by * kB) + 0.5f - ext,
+                                       (float)(bz * kB) + 0.5f - ext);
+        const float3 qhi = make_float3((float)(bx * kB + kB - 1) + 0.5f + ext,
+                                       (float)(by * kB + kB - 1) + 0.5f + ext,
+                                       (float)(bz * kB + kB - 1) + 0.5f + ext);
+        bool overflow = false;
+        for (int pass = 0; pass * 32 < nm; ++pass) {
+            const int slot = pass * 32 + lane;
+            const bool mine = slot < nm;
+            int lin = 0;
+            float3 o = make_float3(0.f, 0.f, 0.f);
+            if (mine) {
+                // position of the slot-th set bit of the brick mask
+                unsigned long long mm = m;
+                int skip = slot;
+                const int lo_cnt = __popc((uint32_t)mm);
+                if (skip >= lo_cnt) {
+                    skip -= lo_cnt;
+                    mm &= 0xffffffff00000000ull;
+                }
+                for (int c = 0; c < skip; ++c) mm &= mm - 1ull;
+                const int bit = __ffsll((long long)mm) - 1;
+                const int i = bx * kB + (bit & 3), j = by * kB + ((bit >> 2) & 3), k = bz * kB + (bit >> 4);
+                lin = (int)(((int64_t)k * a.g.ny + j) * a.g.nx + i);
+                o = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
             }
+            w.origin[lane] = make_float4(o.x, o.y, o.z, 0.f);
+            uint32_t vbest = 0xffffffffu, vfront = 0, vback = 0;
+            for (int r0 = 0; r0 < a.R; r0 += kRaysPerLane) {
+                float3 dir[kRaysPerLane];
+                uint32_t okm = 0;
+#pragma unroll
+                for (int r = 0; r < kRaysPerLane; ++r) {
+                    const int ray = r0 + r;
+                    dir[r] = make_float3(0.f, 0.f, 1.f);
+                    if (mine && ray < a.R) {
+                        if (sphere_dir((uint32_t)lin, a.frame * (uint32_t)a.R + (uint32_t)ray, a.scene, a.k0, a.k1,
+                                       dir[r]))
+                            okm |= 1u << r;
+                        else
+                            ++n_fail;
+                    }
+                    w.dir[r][lane] = make_float4(dir[r].x, dir[r].y, dir[r].z, 0.f);
+                    w.key[r][lane] = ~0ull;
+                }
+                int sp = 0;
+                if (n_leaves > 0) {
+                    if (lane == 0) w.stack[0] = 0;
+                    sp = 1;
+                }
+                __syncwarp();
+                while (sp > 0) {
+                    const int nc = walk_and_stage(nodes, leaves, n_inner, n_leaves, qlo, qhi, w.stack, sp, w.cand, 0,
+                                                  a.tmax, overflow);
+                    int qn = 0;
+                    for (int c = 0; c < nc; ++c) {
+                        uint32_t pm = 0;  // rays of this lane that pass the filters for triangle c
+                        const float4 sph = w.cand[c].sph;
+                        const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
+                        const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
+                        if (okm && dd <= sph.w) {
+                            // a hit point lies within rho of the centre: the line passes within rho of
+                            // it, and the centre is not more than rho behind the origin
+                            const float rho = w.cand[c].e1.w;
+                            const float rho2 = rho * rho;
+#pragma unroll
+                            for (int r = 0; r < kRaysPerLane; ++r) {
+                                const float tc =
+                                    __fmaf_rn(dcx, dir[r].x, __fmaf_rn(dcy, dir[r].y, dcz * dir[r].z));
+                                const float l2 = __fmaf_rn(-tc, tc, dd);
+                                if (l2 <= rho2 && tc >= -rho) pm |= 1u << r;
+                            }
+                            pm &= okm;
+                        }
+                        // enqueue (c, slot, ray) items: warp prefix sum of the lanes' counts
+                        const int cnt = __popc(pm);
+                        int pre = cnt;
+#pragma unroll
+                        for (int off = 1; off < 32; off <<= 1) {
+                            const int u = __shfl_up_sync(0xffffffffu, pre, off);
+                            if (lane >= off) pre += u;
+                        }
+                        const int tot = __shfl_sync(0xffffffffu, pre, 31);
+                        if (tot) {
+                            int pos = qn + pre - cnt;
+                            while (pm) {
+                                const int r = __ffs(pm) - 1;
+                                pm &= pm - 1u;
+                                w.queue[pos++] = ((uint32_t)c << 8) | ((uint32_t)lane << 3) | (uint32_t)r;
+                            }
+                            qn += tot;
+                            __syncwarp();
+                            while (qn >= 32) {
+                                run_item(w, w.queue[qn - 32 + lane], a.tmax);
+                                qn -= 32;
+                                __syncwarp();
+                            }
+                        }
+                    }
+                    if (lane < qn) run_item(w, w.queue[lane], a.tmax);
+                    __syncwarp();
+                }
+                // closest hits of this lane's rays
+#pragma unroll
+                for (int r = 0; r < kRaysPerLane; ++r) {
+                    const unsigned long long key = w.key[r][lane];
+                    if (key != ~0ull) {
+                        vbest = min(vbest, (uint32_t)(key >> 32));
+                        if (key & 1ull) ++vfront; else ++vback;
+                        ++n_hit;
+                    }
+                }
+                __syncwarp();
+            }
+            if (mine) {
+                const uint32_t d = min(dist_bits[lin], vbest);
+                const uint32_t fr = front[lin] + vfront, bk = back[lin] + vback;
+                dist_bits[lin] = d;
+                front[lin] = fr;
+                back[lin] = bk;
+                bool neg = bk > fr;
+                if (fr == bk && a.fallback) {
+                    const int32_t s = nearest[lin];
+                    const int64_t sl2 =
+                        ((int64_t)((s >> 20) & 1023) * a.g.ny + ((s >> 10) & 1023)) * a.g.nx + (s & 1023);
+                    float3 A, B, C;
+                    load_tri(a.verts, a.V, a.tris, rep_tri[sl2], a.g, A, B, C);
+                    const float3 n = cross3(sub3(B, A), sub3(C, A));
+                    neg = dot3(sub3(o, A), n) < 0.0f;
+                }
+                const float df = __uint_as_float(d);
+                sdf[lin] = neg ? -df : df;
+            }
+            __syncwarp();
         }
-        const bool hit = h.id != 0x7fffffff;
-        n_hit += hit;
-        if (grouped) {
-            // reduce the R lanes of each voxel: min t, front and back vote counts
-            uint32_t tb = hit ? __float_as_uint(h.t) : 0xffffffffu;
-            uint32_t nf = (hit && h.front) ? 1u : 0u, nb = (hit && !h.front) ? 1u : 0u;
-            for (int o2 = 1; o2 < a.R; o2 <<= 1) {
-                tb = min(tb, __shfl_xor_sync(0xffffffffu, tb, o2));
-                nf += __shfl_xor_sync(0xffffffffu, nf, o2);
-                nb += __shfl_xor_sync(0xffffffffu, nb, o2);
-            }
-            if (active && (lane % (uint32_t)a.R) == 0) {
-                if (tb != 0xffffffffu) dist_bits[lin] = min(dist_bits[lin], tb);
-                front[lin] += nf;
-                back[lin] += nb;
-            }
-        } else if (active && hit) {
-            atomicMin(dist_bits + lin, __float_as_uint(h.t));
-            atomicAdd(h.front ? front + lin : back + lin, 1u);
-        }
+        n_ovf += overflow ? 1u : 0u;
     }
     if (counters) {
         if (n_hit) atomicAdd(&counters->rays_hit, n_hit);
         if (n_fail) atomicAdd(&counters->rays_failed, n_fail);
-        if (n_ovf) atomicAdd(&counters->stack_overflow, n_ovf);
     }
+    if (lane == 0 && n_ovf) atomicAdd(count + 2, n_ovf);
 }
 
-__global__ void k_finalize(RefineArgs a, const int32_t* __restrict__ list, const uint32_t* __restrict__ count,
-                           const int32_t* __restrict__ nearest, const int32_t* __restrict__ rep_tri,
-                           const uint32_t* __restrict__ dist_bits, const uint32_t* __restrict__ front,
-                           const uint32_t* __restrict__ back, float* __restrict__ sdf, rtsdf_counters* counters) {
-    const uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
-    if (li == 0 && counters) atomicAdd(&counters->masked_voxels, count[0]);
-    if (li >= count[0]) return;
-    const int lin = list[li];
-    const float d = __uint_as_float(dist_bits[lin]);
-    const uint32_t fr = front[lin], bk = back[lin];
-    bool neg = bk > fr;
-    if (fr == bk && a.fallback) {
-        const int32_t s = nearest[lin];
-        const int64_t sl = ((int64_t)((s >> 20) & 1023) * a.g.ny + ((s >> 10) & 1023)) * a.g.nx + (s & 1023);
-        float3 A, B, C;
-        load_tri(a.verts, a.V, a.tris, rep_tri[sl], a.g, A, B, C);
-        const int64_t plane = (int64_t)a.g.nx * a.g.ny;
-        const int k = (int)(lin / plane), rem = (int)(lin - (int64_t)k * plane);
-        const int j = rem / a.g.nx, i = rem - j * a.g.nx;
-        const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
-        const float3 n = cross3(sub3(B, A), sub3(C, A));
-        neg = dot3(sub3(p, A), n) < 0.0f;
-    }
-    sdf[lin] = neg ? -d : d;
+// Masked voxels (set bits over all bricks) and walks that overflowed, to the counters.
+__global__ void k_refine_report(const uint32_t* __restrict__ count, const unsigned long long* __restrict__ bmask,
+                                size_t nb, rtsdf_counters* counters) {
+    uint32_t n = 0;
+    for (size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (size_t)gridDim.x * blockDim.x)
+        n += __popcll(bmask[b]);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&counters->masked_voxels, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && count[2]) atomicAdd(&counters->stack_overflow, count[2]);
 }
 
 rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const int32_t* tris, int32_t T,
@@ -288,21 +491,33 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
     a.scene = p.scene_id;
     a.accumulate = p.accumulate;
     a.fallback = p.sign_fallback;
+    a.nbx = (gh.nx + kB - 1) / kB;
+    a.nby = (gh.ny + kB - 1) / kB;
+    a.nbz = (gh.nz + kB - 1) / kB;
     RefineWs w;
     refine_ws_layout(gh, static_cast<char*>(ws), &w);
-    const int64_t nvox = (int64_t)gh.nx * gh.ny * gh.nz;
     const auto* hdr = static_cast<const BvhHeader*>(bvh);
     const auto* nodes = reinterpret_cast<const BvhNode*>(static_cast<const char*>(bvh) + bvh_nodes_offset());
     const auto* leaves = reinterpret_cast<const BvhLeaf*>(static_cast<const char*>(bvh) + bvh_leaves_offset(T));
     RTSDF_CUDA(cudaMemsetAsync(w.count, 0, 16, s));
-    k_resolve<<<(unsigned)((nvox + 255) / 256), 256, 0, s>>>(a, nearest, rep_tri, dist_bits, front, back, sdf, w.list,
-                                                            w.count);
+    const dim3 rgrid((gh.nx + 31) / 32, a.nby, a.nbz);
+    k_resolve<<<rgrid, 512, 0, s>>>(a, nearest, rep_tri, dist_bits, front, back, sdf, w.bmask, w.blist, w.count);
     RTSDF_LAUNCHED();
-    k_trace<<<num_sms() * 8, 256, 0, s>>>(a, hdr, nodes, leaves, w.list, w.count, dist_bits, front, back, counters);
+    const size_t smem = sizeof(WarpSmem) * (kRefineThreads / 32);
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    RTSDF_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        RTSDF_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[dev] = true;
+    }
+    k_refine<<<num_sms() * 9, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
+                                                       w.count, dist_bits, front, back, sdf, counters);
     RTSDF_LAUNCHED();
-    k_finalize<<<(unsigned)((nvox + 255) / 256), 256, 0, s>>>(a, w.list, w.count, nearest, rep_tri, dist_bits, front,
-                                                             back, sdf, counters);
-    RTSDF_LAUNCHED();
+    if (counters) {
+        k_refine_report<<<num_sms(), 256, 0, s>>>(w.count, w.bmask, nbricks(gh), counters);
+        RTSDF_LAUNCHED();
+    }
     return RTSDF_OK;
 }
 
