@@ -172,6 +172,19 @@ __global__ void k_bvh_leaves(const float* __restrict__ verts, int V, const int32
     leaves[j].v0 = make_float4(a.x, a.y, a.z, __int_as_float(tri));
     leaves[j].e1 = make_float4(e1.x, e1.y, e1.z, 0.0f);
     leaves[j].e2 = make_float4(e2.x, e2.y, e2.z, 0.0f);
+    {
+        const float3 cen = make_float3((a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
+                                       (a.z + b.z + c.z) * (1.0f / 3.0f));
+        const float3 da = sub3(a, cen), db = sub3(b, cen), dc = sub3(c, cen);
+        const float r = sqrtf(fmaxf(fmaxf(dot3(da, da), dot3(db, db)), dot3(dc, dc)));
+        // margin far above the FP32 rounding of any accepted hit point
+        const float pad = 0.01f + 1e-5f * (fabsf(cen.x) + fabsf(cen.y) + fabsf(cen.z) + r);
+        leaves[j].sph = make_float4(cen.x, cen.y, cen.z, r + pad);
+        const float3 n = cross3(e1, e2);
+        const float nl = sqrtf(dot3(n, n));
+        const float3 nu = nl > 0.0f ? make_float3(n.x / nl, n.y / nl, n.z / nl) : make_float3(0.f, 0.f, 0.f);
+        leaves[j].pln = make_float4(nu.x, nu.y, nu.z, dot3(nu, a));
+    }
     float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y), fminf(fminf(a.z, b.z), c.z));
     float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y), fmaxf(fmaxf(a.z, b.z), c.z));
     lo = make_float3(lo.x - pad_of(lo.x), lo.y - pad_of(lo.y), lo.z - pad_of(lo.z));

@@ -26,10 +26,11 @@ namespace rtsdf {
 
 constexpr int kB = 4;                // brick edge (voxels)
 constexpr int kRefineThreads = 64;   // independent warps, one brick each
-constexpr int kCandCapW = 64;        // staged triangles per warp and round
+constexpr int kListCap = 512;        // staged leaves per warp and round
 constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
 constexpr int kRaysPerLane = 8;      // rays of a voxel per group (one lane per voxel)
-constexpr int kQueueCap = 32 + 256;  // queued ray/triangle items per warp
+constexpr int kFilterBatch = 4;      // staged triangles filtered per enqueue
+constexpr int kQueueCap = 32 + 32 * 8 * kFilterBatch;  // queued ray/triangle items per warp
 
 struct RefineWs {
     uint32_t* count;            // [0] active bricks, [1] work counter, [2] walks that overflowed
@@ -149,28 +150,26 @@ __global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __
 
 // ------------------------------------------------------------------ refine
 
-__device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, float3 qlo, float3 qhi) {
-    return lo.x <= qhi.x && hi.x >= qlo.x && lo.y <= qhi.y && hi.y >= qlo.y && lo.z <= qhi.z && hi.z >= qlo.z;
+// Does box [lo, hi] come within `ext` of the box [qlo, qhi] (the voxel centres of a
+// brick)?  Every point a ray of the brick can reach satisfies this, so boxes that
+// fail it hold no triangle any of the brick's rays can hit.
+__device__ __forceinline__ bool box_near(float4 lo, float4 hi, float3 qlo, float3 qhi, float ext2) {
+    const float gx = fmaxf(fmaxf(lo.x - qhi.x, qlo.x - hi.x), 0.0f);
+    const float gy = fmaxf(fmaxf(lo.y - qhi.y, qlo.y - hi.y), 0.0f);
+    const float gz = fmaxf(fmaxf(lo.z - qhi.z, qlo.z - hi.z), 0.0f);
+    return __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz)) <= ext2;
 }
 
-struct Cand {
-    float4 v0;   // xyz, w = triangle id bits
-    float4 e1;
-    float4 e2;
-    float4 sph;  // centre xyz, w = (radius + ray length + margin)^2
-};
-
-// Warp-cooperative walk of the BVH for the query box: pops up to 32 nodes per
-// step from the warp's stack and stages the leaves it reaches; stops when the
-// stack is empty or the staging buffer could overflow on the next step.
-// Returns the new candidate count; *sp_io is the stack depth.
-__device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes, const BvhLeaf* __restrict__ leaves,
-                                              int n_inner, int n_leaves, float3 qlo, float3 qhi, int* stack,
-                                              int& sp, Cand* cand, int nc, float tmax, bool& overflow) {
+// Warp-cooperative walk of the BVH for the query region: pops up to 32 nodes per
+// step from the warp's stack and appends the leaves it reaches to `list`; stops
+// when the stack is empty or the list could overflow on the next step.  Returns
+// the new list length; `sp` is the stack depth.
+__device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes, int n_inner, int n_leaves,
+                                              float3 qlo, float3 qhi, float ext2, int* stack, int& sp,
+                                              int* list, int nc, bool& overflow) {
     const int lane = threadIdx.x & 31;
-    const int nc0 = nc;
     int guard = 0;
-    while (sp > 0 && nc <= kCandCapW - 64) {
+    while (sp > 0 && nc <= kListCap - 64) {
         if (++guard > n_inner + 64) {  // a well-formed tree is exhausted long before
             overflow = true;
             sp = 0;
@@ -188,8 +187,8 @@ __device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes,
             const float4 lo1 = __ldg(&nd->lo1), hi1 = __ldg(&nd->hi1);
             c0 = __float_as_int(lo0.w);
             c1 = __float_as_int(hi0.w);
-            h0 = box_overlap(lo0, hi0, qlo, qhi);
-            h1 = n_leaves > 1 && box_overlap(lo1, hi1, qlo, qhi);
+            h0 = box_near(lo0, hi0, qlo, qhi, ext2);
+            h1 = n_leaves > 1 && box_near(lo1, hi1, qlo, qhi, ext2);
             if (c0 < 0 && ~c0 >= n_leaves) h0 = false;
             if (c1 < 0 && ~c1 >= n_leaves) h1 = false;
         }
@@ -211,16 +210,8 @@ __device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes,
         if (h0 && c0 >= 0) { if (wp < kStackCapW) stack[wp] = c0; ++wp; }
         if (h1 && c1 >= 0) { if (wp < kStackCapW) stack[wp] = c1; ++wp; }
         int wl = nc + pl - nl;
-        if (h0 && c0 < 0) {
-            const BvhLeaf* L = leaves + ~c0;
-            cand[wl].v0 = __ldg(&L->v0); cand[wl].e1 = __ldg(&L->e1); cand[wl].e2 = __ldg(&L->e2);
-            ++wl;
-        }
-        if (h1 && c1 < 0) {
-            const BvhLeaf* L = leaves + ~c1;
-            cand[wl].v0 = __ldg(&L->v0); cand[wl].e1 = __ldg(&L->e1); cand[wl].e2 = __ldg(&L->e2);
-            ++wl;
-        }
+        if (h0 && c0 < 0) list[wl++] = ~c0;
+        if (h1 && c1 < 0) list[wl++] = ~c1;
         if (sp + tot_p > kStackCapW) {
             overflow = true;
             sp = kStackCapW;
@@ -230,28 +221,15 @@ __device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes,
         nc += tot_l;
         __syncwarp();
     }
-    // bounding spheres of the newly staged triangles
-    for (int c = nc0 + lane; c < nc; c += 32) {
-        const float4 v0 = cand[c].v0, e1 = cand[c].e1, e2 = cand[c].e2;
-        const float3 cen = make_float3(v0.x + (e1.x + e2.x) * (1.0f / 3.0f), v0.y + (e1.y + e2.y) * (1.0f / 3.0f),
-                                       v0.z + (e1.z + e2.z) * (1.0f / 3.0f));
-        const float3 a0 = make_float3(v0.x - cen.x, v0.y - cen.y, v0.z - cen.z);
-        const float3 a1 = make_float3(a0.x + e1.x, a0.y + e1.y, a0.z + e1.z);
-        const float3 a2 = make_float3(a0.x + e2.x, a0.y + e2.y, a0.z + e2.z);
-        const float r = sqrtf(fmaxf(fmaxf(dot3(a0, a0), dot3(a1, a1)), dot3(a2, a2)));
-        const float lim = r + tmax + 0.01f + 1e-5f * (fabsf(cen.x) + fabsf(cen.y) + fabsf(cen.z) + r + tmax);
-        cand[c].sph = make_float4(cen.x, cen.y, cen.z, lim * lim);
-        cand[c].e1.w = lim - tmax;  // radius of the sphere any accepted hit point lies in
-    }
-    __syncwarp();
     return nc;
 }
 
 // Per-warp shared state of k_refine.
 struct WarpSmem {
-    Cand cand[kCandCapW];
+    int list[kListCap];             // staged leaves
     int stack[kStackCapW];
-    uint32_t queue[kQueueCap];      // (candidate << 8) | (slot << 3) | ray
+    uint32_t queue[kQueueCap];      // (list index << 8) | (slot << 3) | ray
+    int qn;                         // queued items
     float4 origin[32];              // voxel centres of the pass's slots
     float4 dir[8][32];              // ray directions of the group, [ray][slot]
     unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
@@ -259,11 +237,13 @@ struct WarpSmem {
 
 // Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
 // closest hit per ray (ties to the lower id) is kept with a 64-bit atomicMin.
-__device__ __forceinline__ void run_item(WarpSmem& w, uint32_t item, float tmax) {
+__device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
+                                         float tmax) {
     const int c = (int)(item >> 8), slot = (int)((item >> 3) & 31u), r = (int)(item & 7u);
     const float4 of = w.origin[slot], df = w.dir[r][slot];
     const float3 o = make_float3(of.x, of.y, of.z), d = make_float3(df.x, df.y, df.z);
-    const float4 v0 = w.cand[c].v0, e1f = w.cand[c].e1, e2f = w.cand[c].e2;
+    const BvhLeaf* L = leaves + w.list[c];
+    const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
     const float3 A = make_float3(v0.x, v0.y, v0.z);
     const float3 e1 = make_float3(e1f.x, e1f.y, e1f.z), e2 = make_float3(e2f.x, e2f.y, e2f.z);
     float t;
@@ -276,6 +256,42 @@ __device__ __forceinline__ void run_item(WarpSmem& w, uint32_t item, float tmax)
     }
 }
 
+// Which of this lane's rays can hit the triangle of `leaf`: the (voxel, triangle)
+// pair must be within reach of the bounding sphere; each ray's line must pass
+// within rho of the sphere centre with the centre at most rho behind the origin
+// (off the rho-sphere by more than rho*sqrt(2) that is exactly tc >= sqrt(dd -
+// rho^2); nearer, tc >= -rho is kept, a superset); and the ray must head for the
+// triangle's plane and cross it within the ray length.  All margins exceed the
+// FP32 rounding of both sides, so no triangle the exact test accepts is dropped.
+__device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf, float3 o, uint32_t okm,
+                                                const float2* dx2, const float2* dy2, const float2* dz2,
+                                                float tmax) {
+    const float4 sph = __ldg(&leaf->sph);
+    const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
+    const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
+    const float reach = sph.w + tmax;
+    if (!okm || dd > reach * reach) return 0u;
+    const float4 pl = __ldg(&leaf->pln);
+    const float rho = sph.w;
+    const float rho2 = rho * rho;
+    const float thr = dd > 2.0f * rho2 ? __fsqrt_rn(dd - rho2) * 0.999999f - 1e-4f : -rho;
+    const float sd = pl.w - __fmaf_rn(pl.x, o.x, __fmaf_rn(pl.y, o.y, pl.z * o.z));
+    const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
+    const float asd = fabsf(sd);
+    const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
+    const float2 nx2 = make_float2(pl.x, pl.x), ny2 = make_float2(pl.y, pl.y), nz2 = make_float2(pl.z, pl.z);
+    uint32_t pm = 0;
+#pragma unroll
+    for (int r = 0; r < kRaysPerLane / 2; ++r) {
+        const float2 tc = __ffma2_rn(cx2, dx2[r], __ffma2_rn(cy2, dy2[r], __fmul2_rn(cz2, dz2[r])));
+        const float2 dn = __ffma2_rn(nx2, dx2[r], __ffma2_rn(ny2, dy2[r], __fmul2_rn(nz2, dz2[r])));
+        const bool ok0 = tc.x >= thr && sd * dn.x > -eps && asd <= __fmaf_rn(tmax, fabsf(dn.x), eps);
+        const bool ok1 = tc.y >= thr && sd * dn.y > -eps && asd <= __fmaf_rn(tmax, fabsf(dn.y), eps);
+        pm |= ((ok0 ? 1u : 0u) << (2 * r)) | ((ok1 ? 1u : 0u) << (2 * r + 1));
+    }
+    return pm & okm;
+}
+
 // One warp per brick; lane l owns voxel slot (pass*32 + l) and up to 8 rays of it
 // per group.  For every staged triangle the lane culls the (voxel, triangle) pair
 // by the triangle's bounding sphere grown by the ray length, then each ray by the
@@ -285,7 +301,7 @@ __device__ __forceinline__ void run_item(WarpSmem& w, uint32_t item, float tmax)
 // not diverge.  Both filters are conservative (their margins exceed FP32 rounding
 // of the exact test), so they never drop a triangle the exact test accepts; they
 // may use fused multiply-adds because they decide nothing the oracle decides.
-__global__ void __launch_bounds__(kRefineThreads, 12) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
                                                               const int32_t* __restrict__ nearest,
@@ -305,6 +321,7 @@ __global__ void __launch_bounds__(kRefineThreads, 12) k_refine(RefineArgs a, con
     const uint32_t nact = count[0];
     uint32_t n_hit = 0, n_fail = 0, n_ovf = 0;
     const float ext = a.tmax * 1.00001f + 1e-3f;
+    const uint32_t lt_mask = (1u << lane) - 1u;
 
     while (true) {
         uint32_t wk = 0;
@@ -316,12 +333,21 @@ __global__ void __launch_bounds__(kRefineThreads, 12) k_refine(RefineArgs a, con
         const unsigned long long m = bmask[b];
         const int nm = __popcll(m);
         // every ray of the brick stays inside its voxel centres' box grown by the ray length
-        const float3 qlo = make_float3((float)(bx * kB) + 0.5f - ext, (float)(by * kB) + 0.5f - ext,
-                                       (float)(bz * kB) + 0.5f - ext);
-        const float3 qhi = make_float3((float)(bx * kB + kB - 1) + 0.5f + ext,
-                                       (float)(by * kB + kB - 1) + 0.5f + ext,
-                                       (float)(bz * kB + kB - 1) + 0.5f + ext);
+        const float3 qlo = make_float3((float)(bx * kB) + 0.5f, (float)(by * kB) + 0.5f, (float)(bz * kB) + 0.5f);
+        const float3 qhi = make_float3((float)(bx * kB + kB - 1) + 0.5f, (float)(by * kB + kB - 1) + 0.5f,
+                                       (float)(bz * kB + kB - 1) + 0.5f);
         bool overflow = false;
+        // walk once for the whole brick; the list is reused by every pass and ray
+        // group unless it overflowed, in which case each pass walks again in rounds
+        int sp0 = 0;
+        if (n_leaves > 0) {
+            if (lane == 0) w.stack[0] = 0;
+            sp0 = 1;
+        }
+        __syncwarp();
+        const int nc_all = walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack, sp0, w.list, 0,
+                                          overflow);
+        const bool complete = sp0 == 0;
         for (int pass = 0; pass * 32 < nm; ++pass) {
             const int slot = pass * 32 + lane;
             const bool mine = slot < nm;
@@ -361,61 +387,63 @@ __global__ void __launch_bounds__(kRefineThreads, 12) k_refine(RefineArgs a, con
                     w.dir[r][lane] = make_float4(dir[r].x, dir[r].y, dir[r].z, 0.f);
                     w.key[r][lane] = ~0ull;
                 }
+                float2 dx2[kRaysPerLane / 2], dy2[kRaysPerLane / 2], dz2[kRaysPerLane / 2];
+#pragma unroll
+                for (int r = 0; r < kRaysPerLane / 2; ++r) {
+                    dx2[r] = make_float2(dir[2 * r].x, dir[2 * r + 1].x);
+                    dy2[r] = make_float2(dir[2 * r].y, dir[2 * r + 1].y);
+                    dz2[r] = make_float2(dir[2 * r].z, dir[2 * r + 1].z);
+                }
                 int sp = 0;
-                if (n_leaves > 0) {
+                if (!complete && n_leaves > 0) {
                     if (lane == 0) w.stack[0] = 0;
                     sp = 1;
                 }
                 __syncwarp();
-                while (sp > 0) {
-                    const int nc = walk_and_stage(nodes, leaves, n_inner, n_leaves, qlo, qhi, w.stack, sp, w.cand, 0,
-                                                  a.tmax, overflow);
-                    int qn = 0;
-                    for (int c = 0; c < nc; ++c) {
-                        uint32_t pm = 0;  // rays of this lane that pass the filters for triangle c
-                        const float4 sph = w.cand[c].sph;
-                        const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
-                        const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
-                        if (okm && dd <= sph.w) {
-                            // a hit point lies within rho of the centre: the line passes within rho of
-                            // it, and the centre is not more than rho behind the origin
-                            const float rho = w.cand[c].e1.w;
-                            const float rho2 = rho * rho;
+                bool first = true;
+                while (first || sp > 0) {
+                    first = false;
+                    const int nc = complete ? nc_all
+                                            : walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack,
+                                                             sp, w.list, 0, overflow);
+                    if (lane == 0) w.qn = 0;
+                    __syncwarp();
+                    for (int c0 = 0; c0 < nc; c0 += kFilterBatch) {
+                        // filter kFilterBatch staged triangles (independent work), then each lane
+                        // that has survivors claims queue slots with one shared atomic
+                        uint32_t pm4 = 0;  // bit (j * 8 + r): ray r vs triangle c0 + j
 #pragma unroll
-                            for (int r = 0; r < kRaysPerLane; ++r) {
-                                const float tc =
-                                    __fmaf_rn(dcx, dir[r].x, __fmaf_rn(dcy, dir[r].y, dcz * dir[r].z));
-                                const float l2 = __fmaf_rn(-tc, tc, dd);
-                                if (l2 <= rho2 && tc >= -rho) pm |= 1u << r;
-                            }
-                            pm &= okm;
+                        for (int j = 0; j < kFilterBatch; ++j) {
+                            const int c = c0 + j;
+                            if (c < nc) pm4 |= filter_rays(leaves + w.list[c], o, okm, dx2, dy2, dz2, a.tmax) << (8 * j);
                         }
-                        // enqueue (c, slot, ray) items: warp prefix sum of the lanes' counts
-                        const int cnt = __popc(pm);
-                        int pre = cnt;
-#pragma unroll
-                        for (int off = 1; off < 32; off <<= 1) {
-                            const int u = __shfl_up_sync(0xffffffffu, pre, off);
-                            if (lane >= off) pre += u;
-                        }
-                        const int tot = __shfl_sync(0xffffffffu, pre, 31);
-                        if (tot) {
-                            int pos = qn + pre - cnt;
-                            while (pm) {
-                                const int r = __ffs(pm) - 1;
-                                pm &= pm - 1u;
-                                w.queue[pos++] = ((uint32_t)c << 8) | ((uint32_t)lane << 3) | (uint32_t)r;
+                        if (pm4) {
+                            int pos = atomicAdd(&w.qn, __popc(pm4));
+                            while (pm4) {
+                                const int bit = __ffs(pm4) - 1;
+                                pm4 &= pm4 - 1u;
+                                w.queue[pos++] =
+                                    ((uint32_t)(c0 + (bit >> 3)) << 8) | ((uint32_t)lane << 3) | (uint32_t)(bit & 7);
                             }
-                            qn += tot;
-                            __syncwarp();
+                        }
+                        __syncwarp();
+                        int qn = w.qn;
+                        if (qn >= 32) {
                             while (qn >= 32) {
-                                run_item(w, w.queue[qn - 32 + lane], a.tmax);
+                                run_item(w, leaves, w.queue[qn - 32 + lane], a.tmax);
                                 qn -= 32;
-                                __syncwarp();
                             }
+                            __syncwarp();
+                            if (lane == 0) w.qn = qn;
+                            __syncwarp();
                         }
                     }
-                    if (lane < qn) run_item(w, w.queue[lane], a.tmax);
+                    {
+                        const int qn = w.qn;
+                        if (lane < qn) run_item(w, leaves, w.queue[lane], a.tmax);
+                        __syncwarp();
+                    }
+                    __syncwarp();
                     __syncwarp();
                 }
                 // closest hits of this lane's rays
@@ -511,7 +539,7 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
         RTSDF_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set[dev] = true;
     }
-    k_refine<<<num_sms() * 9, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
+    k_refine<<<num_sms() * 8, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
                                                        w.count, dist_bits, front, back, sdf, counters);
     RTSDF_LAUNCHED();
     if (counters) {

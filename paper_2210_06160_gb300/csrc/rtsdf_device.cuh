@@ -233,9 +233,11 @@ struct alignas(16) BvhNode {
     float4 hi1;
 };
 struct alignas(16) BvhLeaf {
-    float4 v0;  // xyz = vertex A (voxel space), w = triangle id (int bits)
-    float4 e1;  // B - A
-    float4 e2;  // C - A
+    float4 v0;   // xyz = vertex A (voxel space), w = triangle id (int bits)
+    float4 e1;   // B - A
+    float4 e2;   // C - A
+    float4 sph;  // bounding sphere: centroid xyz, w = radius + margin (a superset of the triangle)
+    float4 pln;  // unit normal xyz (0 for a degenerate triangle), w = normal . A
 };
 
 __host__ __device__ inline size_t bvh_nodes_offset() { return sizeof(BvhHeader); }
