@@ -1,0 +1,84 @@
+"""Small, fixed workloads for kernel profiling (ncu), sized so a full capture of one
+launch ends quickly while the kernel sees the benchmark's voxel size and scene.
+
+    python -m paper_2210_06160_gb300.profile_cases jfa
+        voxelize the 400x200x400 room, then run its 10 flooding passes (only the
+        two 128 MB flooding buffers stay resident)
+    python -m paper_2210_06160_gb300.profile_cases refine-subbox [frames]
+        the room's refinement on a 200^3 sub-box at the benchmark's voxel size
+        (same triangles and brick statistics, ~8 M voxels)
+    python -m paper_2210_06160_gb300.profile_cases shadow
+        the 1920x1080 shadow raymarch of the room on its rebuilt 400x200x400
+        field (only the field and the receivers stay resident)
+"""
+from __future__ import annotations
+
+import dataclasses
+import sys
+
+import torch
+
+from paper_2210_06160_gb300 import build
+from paper_2210_06160_gb300 import rtsdf as rt
+from paper_2210_06160_gb300 import scenes
+
+
+def case_jfa() -> None:
+    sc = scenes.scene_room(shadow_w=64, shadow_h=36)
+    g = rt.make_grid(sc.grid)
+    v, t = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda()
+    seed = torch.empty(sc.grid.shape_zyx, dtype=torch.int32, device="cuda")
+    rep = torch.empty_like(seed)
+    ws = torch.empty(rt.rtsdf_voxelize_workspace(len(sc.tris), g), dtype=torch.uint8, device="cuda")
+    rt.rtsdf_voxelize(v, t, g, seed, rep, ws)
+    del ws, rep
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    out = rt.rtsdf_jfa(g, seed, torch.empty_like(seed), sc.jfa_steps)
+    torch.cuda.synchronize()
+    print("jfa ok", int((out >= 0).sum()))
+
+
+def case_refine_subbox(frames: int = 3) -> None:
+    sc = scenes.scene_room(shadow_w=64, shadow_h=36)
+    g = scenes.Grid(200, 200, 200, (0.5, 0.0, 0.5), 0.005)
+    steps = scenes.jfa_steps(g, extra_one=True)
+    v, t = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda()
+    P = rt.Pipeline(g, len(sc.verts), len(sc.tris))
+    for f in range(frames):
+        P.rebuild(v, t, steps, rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f, accumulate=f > 0)))
+    torch.cuda.synchronize()
+    print("refine-subbox ok", rt.counters_dict(P.counters))
+
+
+def case_shadow() -> None:
+    sc = scenes.scene_room()
+    v, t = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda()
+    P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris))
+    for f in range(2):
+        P.rebuild(v, t, sc.jfa_steps,
+                  rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f, accumulate=f > 0)))
+    sdf = P.sdf.clone()
+    del P
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    pos, nrm = torch.from_numpy(sc.recv_pos).cuda(), torch.from_numpy(sc.recv_nrm).cuda()
+    vis = torch.empty(len(sc.recv_pos), dtype=torch.float32, device="cuda")
+    g, sp = rt.make_grid(sc.grid), rt.make_shadow_params(sc.shadow)
+    for _ in range(3):
+        rt.rtsdf_shadow(g, sdf, pos, nrm, sp, vis)
+    torch.cuda.synchronize()
+    print("shadow ok", float(vis.mean()))
+
+
+if __name__ == "__main__":
+    build.build()
+    which = sys.argv[1] if len(sys.argv) > 1 else "jfa"
+    if which == "jfa":
+        case_jfa()
+    elif which == "shadow":
+        case_shadow()
+    elif which == "refine-subbox":
+        case_refine_subbox(int(sys.argv[2]) if len(sys.argv) > 2 else 3)
+    else:
+        raise SystemExit(f"unknown case {which}")

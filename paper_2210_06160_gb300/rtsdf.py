@@ -228,7 +228,9 @@ class Pipeline:
         self.buf_a = torch.empty(shp, **i32)
         self.buf_b = torch.empty(shp, **i32)
         self.rep_tri = torch.empty(shp, **i32)
-        self.dist_bits = torch.zeros(shp, **i32)
+        # refine state of "no earlier frame": distance +inf, no votes, so that the
+        # first call may already accumulate
+        self.dist_bits = torch.full(shp, 0x7F800000, **i32)
         self.front = torch.zeros(shp, **i32)
         self.back = torch.zeros(shp, **i32)
         self.sdf = torch.empty(shp, dtype=torch.float32, device=dev)
