@@ -145,7 +145,7 @@ def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
     masked = np.flatnonzero(mask.ravel()).astype(np.int32)
     nsub = max(1, min(len(masked), 48 if len(sc.tris) > 10000 else 4096))
     sub = masked[:: max(1, len(masked) // nsub)][:nsub]
-    d, f, b = (x.ravel() for x in oracle.init_refine_state(u_c, mask))
+    d, f, b = (x.ravel() for x in oracle.init_refine_state(u_c, mask)[:3])
     t0 = time.perf_counter()
     oracle.refine_voxels(g, vv, sc.tris, sub, rp, 0, d, f, b)
     t["refine"] = (time.perf_counter() - t0) * len(masked) / max(1, len(sub))

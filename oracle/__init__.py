@@ -17,7 +17,7 @@ import threading
 import numpy as np
 
 _DIR = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_DIR, "rtsdf_oracle.c")
+_SRCS = [os.path.join(_DIR, "rtsdf_oracle.c"), os.path.join(_DIR, "rtsdf_oracle_adjoint.c")]
 _LIB = os.path.join(_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -28,10 +28,10 @@ EMPTY = -1
 def build(force: bool = False) -> str:
     """Compile the oracle (FP32 without contraction, OpenMP over independent voxels)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_DIR, "rtsdf_oracle.h"))):
+            [os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(os.path.join(_DIR, "rtsdf_oracle.h"))]):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-                               "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+                               "-std=c11", "-shared", "-fPIC", "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -63,12 +63,18 @@ def lib():
                 "or_philox4x32_10": (None, [P, P, P]),
                 "or_sphere_dir": (C.c_int, [u32, u32, u32, P, P]),
                 "or_ray_tri": (C.c_int, [P, P, P, P, P, f32, P, P]),
-                "or_refine_voxels": (i64, [G, P, i32, P, i32, P, i64, i32, f32, P, u32, u32, P, P, P]),
+                "or_refine_voxels": (i64, [G, P, i32, P, i32, P, i64, i32, f32, P, u32, u32, P, P, P, P, P]),
                 "or_vote_sign": (C.c_int, [u32, u32, P, P, P, P, C.c_int]),
                 "or_finalize": (None, [G, P, P, P, P, P, P, P, P, P, f32, C.c_int, P]),
                 "or_trilinear": (f32, [G, P, f32, f32, f32]),
                 "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P]),
                 "or_num_threads": (C.c_int, []),
+                "or_frozen_sources": (None, [G, P, P, P, P, P, P, P, P, P, P, u32, C.c_int, P]),
+                "or_frozen_sdf_f64": (None, [G, P, P, P, C.c_double, P]),
+                "or_frozen_sdf_backward_f64": (None, [G, P, P, P, C.c_double, P, P]),
+                "or_sample_loss_f64": (C.c_double, [G, P, P, i32, P, P]),
+                "or_shadow_loss_f64": (C.c_double, [G, P, P, P, P, i32, P, P, f32, i32, f32, f32, f32, f32, f32,
+                                                    P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -182,16 +188,19 @@ def resolve(grid, vv, tris, nearest, rep_tri, mask_vox: float):
     return u_c, mask
 
 
-def refine_voxels(grid, vv, tris, vox, rp, frame: int, dist_bits, front, back) -> int:
-    """Sec. 2.1 on the listed voxels; dist_bits/front/back are updated in place."""
+def refine_voxels(grid, vv, tris, vox, rp, frame: int, dist_bits, front, back, win_ray=None, win_tri=None) -> int:
+    """Sec. 2.1 on the listed voxels; dist_bits/front/back (and the winner record
+    win_ray/win_tri when given) are updated in place."""
     vv, t, vox = _f32(vv), _i32(tris), _i32(vox)
     key = np.array(rp.key, dtype=np.uint32)
     for a in (dist_bits, front, back):
         assert a.dtype == np.uint32 and a.flags["C_CONTIGUOUS"]
+    wr = None if win_ray is None else _p(win_ray)
+    wt = None if win_tri is None else _p(win_tri)
     return int(lib().or_refine_voxels(C.byref(_g(grid)), _p(vv), len(vv), _p(t), len(t), _p(vox),
                                       len(vox), int(rp.rays_per_voxel), float(rp.max_ray_vox),
                                       _p(key), frame & 0xFFFFFFFF, rp.scene_id & 0xFFFFFFFF,
-                                      _p(dist_bits), _p(front), _p(back)))
+                                      _p(dist_bits), _p(front), _p(back), wr, wt))
 
 
 def finalize(grid, vv, tris, nearest, rep_tri, mask, u_c, dist_bits, front, back, rp) -> np.ndarray:
@@ -218,15 +227,24 @@ def shadow(grid, sdf, pos, nrm, sp) -> np.ndarray:
 def init_refine_state(u_c, mask, state=None, accumulate=False):
     """Refinement state before a frame's rays: masked voxels start from the coarse
     distance (or the smaller of it and the accumulated distance), counts from zero
-    (or the accumulated counts); unmasked voxels hold the coarse distance, no votes."""
+    (or the accumulated counts); unmasked voxels hold the coarse distance, no votes.
+    With a 5-tuple state (dist, front, back, win_ray, win_tri) the winner record
+    follows: the coarse source wins when it sets the distance."""
     d0 = u_c.view(np.uint32).copy()
+    none_ray = np.full_like(d0, 0xFFFFFFFF)
+    none_tri = np.full(d0.shape, -1, dtype=np.int32)
     if state is None or not accumulate:
-        return d0, np.zeros_like(d0), np.zeros_like(d0)
-    dist, fr, bk = state
+        return d0, np.zeros_like(d0), np.zeros_like(d0), none_ray, none_tri
+    dist, fr, bk = state[:3]
+    wr = state[3] if len(state) > 3 else none_ray
+    wt = state[4] if len(state) > 4 else none_tri
     m = mask.astype(bool)
-    dist = np.where(m, np.minimum(dist.view(np.float32), u_c).view(np.uint32), d0)
+    coarse_wins = m & (d0 < dist)
+    dist = np.where(m, np.minimum(dist, d0), d0)
+    wr = np.where(coarse_wins | ~m, 0xFFFFFFFF, wr).astype(np.uint32)
+    wt = np.where(coarse_wins | ~m, -1, wt).astype(np.int32)
     return (np.ascontiguousarray(dist, dtype=np.uint32), np.where(m, fr, 0).astype(np.uint32),
-            np.where(m, bk, 0).astype(np.uint32))
+            np.where(m, bk, 0).astype(np.uint32), np.ascontiguousarray(wr), np.ascontiguousarray(wt))
 
 
 def rebuild(scene, frames: int | None = None, frame0: int = 0, voxel_subset=None):
@@ -246,10 +264,66 @@ def rebuild(scene, frames: int | None = None, frame0: int = 0, voxel_subset=None
     nf = scene.frames if frames is None else frames
     for f in range(nf):
         state = init_refine_state(u_c, mask, state, accumulate=rp.accumulate)
-        dist, fr, bk = (a.ravel() for a in state)
-        refine_voxels(g, vv, scene.tris, todo, rp, frame0 + f, dist, fr, bk)
-        state = (dist.reshape(g.shape_zyx), fr.reshape(g.shape_zyx), bk.reshape(g.shape_zyx))
-    dist, fr, bk = state
+        dist, fr, bk, wr, wt = (a.ravel() for a in state)
+        refine_voxels(g, vv, scene.tris, todo, rp, frame0 + f, dist, fr, bk, wr, wt)
+        state = tuple(a.reshape(g.shape_zyx) for a in (dist, fr, bk, wr, wt))
+    dist, fr, bk, wr, wt = state
     sdf = finalize(g, vv, scene.tris, nearest, rep, mask, u_c, dist, fr, bk, rp)
     return dict(vv=vv, seed=seed, rep_tri=rep, skipped=skipped, nearest=nearest, u_c=u_c,
-                mask=mask, masked=masked, refined=todo, dist_bits=dist, front=fr, back=bk, sdf=sdf)
+                mask=mask, masked=masked, refined=todo, dist_bits=dist, front=fr, back=bk,
+                win_ray=wr, win_tri=wt, sdf=sdf)
+
+
+# ------------------------------------------------------------------ adjoint (FP64)
+
+SRC_DTYPE = np.dtype([("kind", np.int32), ("tri", np.int32), ("sign", np.float32), ("dir", np.float32, (3,))])
+
+
+def frozen_sources(grid, vv, tris, nearest, rep_tri, mask, front, back, win_ray, win_tri, rp) -> np.ndarray:
+    """Every discrete choice of the forward, per voxel (kind, triangle, sign, ray dir)."""
+    out = np.zeros(grid.nvox, dtype=SRC_DTYPE)
+    key = np.array(rp.key, dtype=np.uint32)
+    arrs = [_f32(vv), _i32(tris), _i32(nearest), _i32(rep_tri), np.ascontiguousarray(mask, dtype=np.uint8),
+            np.ascontiguousarray(front, dtype=np.uint32), np.ascontiguousarray(back, dtype=np.uint32),
+            np.ascontiguousarray(win_ray, dtype=np.uint32), _i32(win_tri)]
+    lib().or_frozen_sources(C.byref(_g(grid)), *[_p(a) for a in arrs], _p(key), rp.scene_id & 0xFFFFFFFF,
+                            int(bool(rp.sign_fallback)), _p(out))
+    return out
+
+
+def frozen_sdf_f64(grid, verts64, tris, src, beta: float) -> np.ndarray:
+    v = np.ascontiguousarray(verts64, dtype=np.float64)
+    out = np.empty(grid.nvox, dtype=np.float64)
+    lib().or_frozen_sdf_f64(C.byref(_g(grid)), _p(v), _p(_i32(tris)), _p(src), float(beta), _p(out))
+    return out
+
+
+def frozen_sdf_backward_f64(grid, verts64, tris, src, beta: float, gsdf) -> np.ndarray:
+    v = np.ascontiguousarray(verts64, dtype=np.float64)
+    g = np.ascontiguousarray(gsdf, dtype=np.float64).ravel()
+    out = np.zeros_like(v)
+    lib().or_frozen_sdf_backward_f64(C.byref(_g(grid)), _p(v), _p(_i32(tris)), _p(src), float(beta), _p(g),
+                                     _p(out))
+    return out
+
+
+def sample_loss_f64(grid, sdf64, pts, target, gsdf=None) -> float:
+    s = np.ascontiguousarray(sdf64, dtype=np.float64).ravel()
+    pts, target = _f32(pts), _f32(target)
+    return float(lib().or_sample_loss_f64(C.byref(_g(grid)), _p(s), _p(pts), len(pts), _p(target),
+                                          None if gsdf is None else _p(gsdf)))
+
+
+def shadow_loss_f64(grid, sdf32, sdf64, pos, nrm, light, sp, target, gsdf=None, gl=None,
+                    light_decide=None) -> float:
+    """The frozen-control shadow loss; the control flow is that of the FP32 march
+    toward `light_decide` (default: `light` in FP32)."""
+    s32 = _f32(sdf32).ravel()
+    s64 = np.ascontiguousarray(sdf64, dtype=np.float64).ravel()
+    pos, nrm, target = _f32(pos), _f32(nrm), _f32(target)
+    l = np.ascontiguousarray(light, dtype=np.float64)
+    ld = _f32(light if light_decide is None else light_decide)
+    return float(lib().or_shadow_loss_f64(
+        C.byref(_g(grid)), _p(s32), _p(s64), _p(pos), _p(nrm), len(pos), _p(ld), _p(l), float(sp.k), int(sp.steps),
+        float(sp.max_step_vox), float(sp.start_offset_vox), float(sp.normal_offset_vox), float(sp.hit_eps_vox),
+        float(sp.bias_vox), _p(target), None if gsdf is None else _p(gsdf), None if gl is None else _p(gl)))

@@ -385,7 +385,8 @@ int or_ray_tri(const float o[3], const float d[3], const float* A, const float* 
 int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int32_t* tris, int32_t T,
                          const int32_t* vox, int64_t n, int32_t R, float tmax,
                          const uint32_t key[2], uint32_t frame, uint32_t scene,
-                         uint32_t* dist_bits, uint32_t* front, uint32_t* back) {
+                         uint32_t* dist_bits, uint32_t* front, uint32_t* back,
+                         uint32_t* win_ray, int32_t* win_tri) {
     uint8_t* ok = (uint8_t*)malloc((size_t)(T > 0 ? T : 1));
     for (int32_t t = 0; t < T; ++t) ok[t] = (uint8_t)tri_valid(vv, V, tris, t);
     int64_t failed = 0;
@@ -396,14 +397,20 @@ int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int
         const float o[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};
         float dist = bitsf(dist_bits[lin]);
         uint32_t fr = front[lin], bk = back[lin];
+        /* closest hit over this call's rays: (t, triangle) ordered, first ray on ties */
+        float fbest = INFINITY;
+        int32_t fbest_tri = -1;
+        uint32_t fbest_ray = 0xFFFFFFFFu;
         for (int32_t r = 0; r < R; ++r) {
             float dir[3];
-            if (or_sphere_dir((uint32_t)lin, frame * (uint32_t)R + (uint32_t)r, scene, key, dir) < 0) {
+            const uint32_t ray = frame * (uint32_t)R + (uint32_t)r;
+            if (or_sphere_dir((uint32_t)lin, ray, scene, key, dir) < 0) {
                 ++failed;
                 continue;
             }
             float best = INFINITY;
             int best_front = 0, hit = 0;
+            int32_t best_tri = -1;
             for (int32_t t = 0; t < T; ++t) {
                 if (!ok[t]) continue;
                 const int32_t* tr = tris + 3 * (int64_t)t;
@@ -414,13 +421,23 @@ int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int
                     tt < best) { /* ascending ids: strict < keeps the lower id on ties */
                     best = tt;
                     best_front = f;
+                    best_tri = t;
                     hit = 1;
                 }
             }
             if (hit) {
-                if (best < dist) dist = best;
+                if (best < fbest || (best == fbest && best_tri < fbest_tri)) {
+                    fbest = best;
+                    fbest_tri = best_tri;
+                    fbest_ray = ray;
+                }
                 if (best_front) ++fr; else ++bk;
             }
+        }
+        if (fbest < dist) {
+            dist = fbest;
+            if (win_ray) win_ray[lin] = fbest_ray;
+            if (win_tri) win_tri[lin] = fbest_tri;
         }
         dist_bits[lin] = fbits(dist);
         front[lin] = fr;

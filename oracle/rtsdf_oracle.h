@@ -77,11 +77,15 @@ int or_ray_tri(const float o[3], const float d[3], const float* a, const float* 
  * triangles.  For voxel vox[i], rays r = 0..R-1 get ray id frame*R + r; each ray's
  * closest hit (ties to the lower triangle id) lowers dist and votes front/back.
  * dist/front/back hold the incoming state (float bits) and are updated in place.
+ * When this call's closest hit (t, then triangle id, then first ray) lowers dist,
+ * win_ray/win_tri (may be NULL) record that ray id and triangle: the frozen source
+ * of the refined distance used by the adjoint.
  * Returns the number of rays whose direction could not be drawn. */
 int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int32_t* tris, int32_t T,
                          const int32_t* vox, int64_t n, int32_t R, float tmax,
                          const uint32_t key[2], uint32_t frame, uint32_t scene,
-                         uint32_t* dist_bits, uint32_t* front, uint32_t* back);
+                         uint32_t* dist_bits, uint32_t* front, uint32_t* back,
+                         uint32_t* win_ray, int32_t* win_tri);
 
 /* Sign of a refined voxel (Sec. 2.1): negative iff back > front; on a tie the side
  * of the representative triangle's plane decides when fallback != 0. Returns -1/+1. */
@@ -104,6 +108,45 @@ float or_trilinear(const or_grid* g, const float* sdf, float qx, float qy, float
 void or_shadow(const or_grid* g, const float* sdf, const float* pos, const float* nrm, int32_t P,
                const float light_dir[3], float k, int32_t steps, float max_step, float start_off,
                float normal_off, float hit_eps, float bias, float* vis);
+
+/* ------------------------------------------------------------------ adjoint (FP64) */
+
+/* Frozen source of a voxel's field value (rtsdf_oracle_adjoint.c). */
+enum { OR_SRC_CONST = 0, OR_SRC_COARSE_UNMASKED = 1, OR_SRC_COARSE_MASKED = 2, OR_SRC_RAY = 3 };
+typedef struct {
+    int32_t kind;  /* OR_SRC_* */
+    int32_t tri;   /* representative triangle (coarse) or hit triangle (ray) */
+    float sign;    /* vote sign of a masked voxel */
+    float dir[3];  /* direction of the winning ray */
+} or_src;
+
+/* Freezes every discrete choice of a forward pass: flooded seed's representative
+ * triangle, mask, vote sign and the source of a refined distance (win_ray ==
+ * 0xFFFFFFFF: the coarse closest point; else that ray's hit of win_tri). */
+void or_frozen_sources(const or_grid* g, const float* vv, const int32_t* tris, const int32_t* nearest,
+                       const int32_t* rep_tri, const uint8_t* mask, const uint32_t* front, const uint32_t* back,
+                       const uint32_t* win_ray, const int32_t* win_tri, const uint32_t key[2], uint32_t scene,
+                       int fallback, or_src* out);
+
+/* The frozen field in FP64 for world-space vertices (voxel units) and the
+ * accumulation of dL/d(world vertex) from dL/d(field). */
+void or_frozen_sdf_f64(const or_grid* g, const double* verts, const int32_t* tris, const or_src* src, double beta,
+                       double* sdf);
+void or_frozen_sdf_backward_f64(const or_grid* g, const double* verts, const int32_t* tris, const or_src* src,
+                                double beta, const double* gsdf, double* gverts);
+
+/* sum_m (trilinear(field, pts_m) - target_m)^2 in FP64; adds dL/d(field) when gsdf != NULL. */
+double or_sample_loss_f64(const or_grid* g, const double* sdf, const float* pts, int32_t M, const float* target,
+                          double* gsdf);
+
+/* sum_p (vis_p - target_p)^2 of the soft-shadow raymarch with the control flow of
+ * the FP32 march on sdf32 toward l_decide and the values of the FP64 field sdf
+ * toward l; adds dL/d(field) and dL/d(light direction l, unnormalised) when the
+ * pointers are not NULL. */
+double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sdf, const float* pos,
+                          const float* nrm, int32_t P, const float l_decide[3], const double l[3], float k,
+                          int32_t steps, float max_step, float start_off, float normal_off, float hit_eps,
+                          float bias, const float* target, double* gsdf, double* gl);
 
 /* Helpers for the tests: number of OpenMP threads the oracle uses. */
 int or_num_threads(void);

@@ -58,10 +58,10 @@ def room():
     state = None
     for f in range(FRAMES):
         state = oracle.init_refine_state(u_c, mask, state, accumulate=f > 0)
-        d, fr, bk = (a.ravel() for a in state)
-        oracle.refine_voxels(g, vv, sc.tris, sample, dataclasses.replace(rp, frame_index=f), f, d, fr, bk)
-        state = (d.reshape(g.shape_zyx), fr.reshape(g.shape_zyx), bk.reshape(g.shape_zyx))
-    d, fr, bk = state
+        d, fr, bk, wr, wt = (a.ravel() for a in state)
+        oracle.refine_voxels(g, vv, sc.tris, sample, dataclasses.replace(rp, frame_index=f), f, d, fr, bk, wr, wt)
+        state = tuple(a.reshape(g.shape_zyx) for a in (d, fr, bk, wr, wt))
+    d, fr, bk = state[:3]
     sdf = oracle.finalize(g, vv, sc.tris, o_near, o_rep, mask, u_c, d, fr, bk, rp)
     ref = dict(seed=o_seed, rep_tri=o_rep, nearest=o_near, mask=mask, u_c=u_c, sample=sample,
                dist_bits=d.ravel(), front=fr.ravel(), back=bk.ravel(), sdf=sdf)

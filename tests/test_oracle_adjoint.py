@@ -1,0 +1,111 @@
+"""Pins of the FP64 frozen-choice adjoint (oracle/rtsdf_oracle_adjoint.c) against
+central finite differences of the same frozen FP64 losses, and checks of the
+winner record kept by the oracle's refinement."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2210_06160_gb300 import scenes
+
+
+def _adjoint_scene(seed=3, n=24):
+    """A sphere and a rotated box in a small grid (a miniature of the differentiation workload)."""
+    rng = np.random.default_rng(seed)
+    Vs, Ts = scenes.icosphere(2)
+    Vb, Tb = scenes.box_mesh()
+    R = scenes.random_rotation(rng)
+    V, T = scenes.merge([(Vs * 0.22 + [0.42, 0.5, 0.5], Ts), ((Vb * 0.12) @ R.T + [0.72, 0.45, 0.55], Tb)])
+    g = scenes.Grid(n, n, n, (0.0, 0.0, 0.0), 1.0 / n)
+    rp = scenes.RefineParams(mask_vox=2.5, rays_per_voxel=8, max_ray_vox=6.0, beta_vox=1.0, key=(9, 1))
+    sp = scenes.ShadowParams(light_dir=(0.35, 1.0, 0.15), k=6.0, steps=48, max_step_vox=1.5,
+                             start_offset_vox=1.0, normal_offset_vox=1.0)
+    pos, nrm = scenes.receivers_plane(0.12, 0.05, 0.95, 0.05, 0.95, 24, 24)
+    return scenes.Scene("adjoint", V.astype(np.float32), T, g, rp, sp, scenes.jfa_steps(g), 2, pos, nrm)
+
+
+@pytest.fixture(scope="module")
+def frozen(orc):
+    sc = _adjoint_scene()
+    r = orc.rebuild(sc)
+    src = orc.frozen_sources(sc.grid, r["vv"], sc.tris, r["nearest"], r["rep_tri"], r["mask"], r["front"],
+                             r["back"], r["win_ray"], r["win_tri"], sc.refine)
+    return sc, r, src
+
+
+def test_winner_record_reproduces_refined_distance(orc, frozen):
+    """The recorded source of each masked voxel reproduces its FP32 refined distance:
+    the coarse closest point, or the recorded ray's hit of the recorded triangle."""
+    sc, r, src = frozen
+    m = r["mask"].ravel().astype(bool)
+    dist = r["dist_bits"].ravel().view(np.float32)
+    f64 = orc.frozen_sdf_f64(sc.grid, sc.verts.astype(np.float64), sc.tris, src, sc.refine.beta_vox)
+    sign = src["sign"]
+    kinds = src["kind"][m]
+    assert (kinds == 3).sum() > 50 and (kinds == 2).sum() > 10   # both sources occur
+    np.testing.assert_allclose(np.abs(f64[m]), dist[m], rtol=2e-5, atol=2e-5)
+    np.testing.assert_allclose(np.sign(f64[m]), sign[m])
+    # and the whole frozen field equals the FP32 field
+    np.testing.assert_allclose(f64, r["sdf"].ravel(), rtol=2e-5, atol=2e-5)
+
+
+def _loss(orc, sc, src, verts64, light, pts, s_tgt, v_tgt, sdf32):
+    """The frozen FP64 loss; the raymarch control flow stays that of the unperturbed light."""
+    f = orc.frozen_sdf_f64(sc.grid, verts64, sc.tris, src, sc.refine.beta_vox)
+    return (orc.sample_loss_f64(sc.grid, f, pts, s_tgt)
+            + orc.shadow_loss_f64(sc.grid, sdf32, f, sc.recv_pos, sc.recv_nrm, light, sc.shadow, v_tgt,
+                                  light_decide=sc.shadow.light_dir))
+
+
+def test_fp64_adjoint_matches_central_differences(orc, frozen):
+    sc, r, src = frozen
+    rng = np.random.default_rng(11)
+    g = sc.grid
+    pts = rng.uniform(0.05, 0.95, (400, 3)).astype(np.float32)
+    V0 = sc.verts.astype(np.float64)
+    light = np.array(sc.shadow.light_dir, np.float64)
+    sdf32 = r["sdf"]
+    f0 = orc.frozen_sdf_f64(g, V0, sc.tris, src, sc.refine.beta_vox)
+    s_tgt = (rng.normal(0, 0.3, len(pts))).astype(np.float32)
+    v_tgt = rng.uniform(0, 1, len(sc.recv_pos)).astype(np.float32)
+    # analytic gradient
+    gsdf = np.zeros(g.nvox)
+    gl = np.zeros(3)
+    orc.sample_loss_f64(g, f0, pts, s_tgt, gsdf)
+    orc.shadow_loss_f64(g, sdf32, f0, sc.recv_pos, sc.recv_nrm, light, sc.shadow, v_tgt, gsdf, gl)
+    gV = orc.frozen_sdf_backward_f64(g, V0, sc.tris, src, sc.refine.beta_vox, gsdf)
+    assert np.abs(gV).max() > 0 and np.abs(gl).max() > 0
+    # central differences of the frozen FP64 loss on the coordinates that matter most
+    h = 1e-5
+    flat = np.argsort(-np.abs(gV.ravel()))[:24]
+    for idx in flat:
+        Vp, Vm = V0.copy().ravel(), V0.copy().ravel()
+        Vp[idx] += h
+        Vm[idx] -= h
+        fd = (_loss(orc, sc, src, Vp.reshape(-1, 3), light, pts, s_tgt, v_tgt, sdf32)
+              - _loss(orc, sc, src, Vm.reshape(-1, 3), light, pts, s_tgt, v_tgt, sdf32)) / (2 * h)
+        assert abs(fd - gV.ravel()[idx]) <= 1e-4 * max(1.0, abs(fd)), (idx, fd, gV.ravel()[idx])
+    for a in range(3):
+        lp, lm = light.copy(), light.copy()
+        lp[a] += h
+        lm[a] -= h
+        fd = (_loss(orc, sc, src, V0, lp, pts, s_tgt, v_tgt, sdf32)
+              - _loss(orc, sc, src, V0, lm, pts, s_tgt, v_tgt, sdf32)) / (2 * h)
+        assert abs(fd - gl[a]) <= 1e-4 * max(1.0, abs(fd)), (a, fd, gl[a])
+
+
+def test_accumulated_winner_follows_minimum(orc):
+    """Across frames the winner changes exactly when the distance drops."""
+    sc = _adjoint_scene(seed=5)
+    sc = dataclasses.replace(sc, refine=dataclasses.replace(sc.refine, accumulate=True, rays_per_voxel=3))
+    r1 = orc.rebuild(sc, frames=1)
+    r3 = orc.rebuild(sc, frames=3)
+    m = r1["mask"].astype(bool)
+    d1 = r1["dist_bits"].view(np.float32)[m]
+    d3 = r3["dist_bits"].view(np.float32)[m]
+    assert np.all(d3 <= d1)
+    changed = d3 < d1
+    assert changed.sum() > 0
+    assert np.all(r3["win_ray"][m][changed] >= 3)          # a ray of frames 1..2 (ray ids frame*R + r)
+    same = ~changed
+    np.testing.assert_array_equal(r3["win_ray"][m][same], r1["win_ray"][m][same])

@@ -497,7 +497,7 @@ def test_refine_converges_with_accumulated_rays(orc):
     u_c, mask = orc.resolve(g, V, T, near, rep, 2.0)
     rp = scenes.RefineParams(rays_per_voxel=64, max_ray_vox=8.0, key=(3, 4), accumulate=True)
     vox = np.flatnonzero(mask.ravel()).astype(np.int32)
-    dist, fr, bk = (a.ravel() for a in orc.init_refine_state(u_c, mask))
+    dist, fr, bk = (a.ravel() for a in orc.init_refine_state(u_c, mask)[:3])
     prev = dist.view(np.float32).copy()
     for f in range(8):
         orc.refine_voxels(g, V, T, vox, rp, f, dist, fr, bk)
