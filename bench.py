@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--workload", default="room", choices=["room", "tiny"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true", help="skip the backward and batched sections")
     return ap.parse_args()
 
 
@@ -120,9 +121,9 @@ class ClockSampler:
 
 def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
     """The oracle as it stands on a bounded sample of one frame, scaled to a full
-    frame: full voxelize, 2 of the JFA passes (scaled to all), full resolve,
-    ray sampling of a subset of masked voxels (scaled to all masked voxels), and
-    the shadow of a subset of receivers (scaled to all)."""
+    frame: full voxelize, all JFA passes, full resolve, ray sampling of a subset of
+    masked voxels (scaled to all masked voxels), and the shadow of a subset of
+    receivers (scaled to all)."""
     import numpy as np
 
     import oracle
@@ -132,13 +133,9 @@ def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
     vv = oracle.to_voxel(sc.verts, g)
     seed, rep, _ = oracle.voxelize(vv, sc.tris, g)
     t["voxelize"] = time.perf_counter() - t0
-    npass = min(2, len(sc.jfa_steps))
     t0 = time.perf_counter()
-    a = seed
-    for k in sc.jfa_steps[-npass:]:
-        a = oracle.jfa_pass(g, a, k)
-    t["jfa"] = (time.perf_counter() - t0) * len(sc.jfa_steps) / npass
-    near = oracle.jfa(g, seed, sc.jfa_steps) if sc.grid.nvox <= 64 ** 3 else a
+    near = oracle.jfa(g, seed, sc.jfa_steps)
+    t["jfa"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     u_c, mask = oracle.resolve(g, vv, sc.tris, near, rep, rp.mask_vox)
     t["resolve"] = time.perf_counter() - t0
@@ -156,7 +153,7 @@ def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
     t["shadow"] = (time.perf_counter() - t0) * len(sc.recv_pos) / npix
     total_ms = 1e3 * sum(t.values())
     return {"value": total_ms, "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"full voxelize + resolve; {npass} of {len(sc.jfa_steps)} JFA passes scaled; ray sampling "
+            "sample": (f"full voxelize + JFA ({len(sc.jfa_steps)} passes) + resolve; ray sampling "
                        f"of {len(sub)} of {len(masked)} masked voxels scaled; shadow of {npix} of "
                        f"{len(sc.recv_pos)} receivers scaled"),
             "stage_s": {k: round(v, 3) for k, v in t.items()}}
@@ -189,6 +186,101 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU path
+
+def bench_backward(dev, steps: int = 10, warmup: int = 3) -> dict:
+    """Forward + adjoint on the 128^3 differentiation workload (8 icospheres s3 +
+    2 boxes, 65,536 field samples, 512x512 shadow image, 1 frame of 8 rays), against
+    the plain forward (untracked refine) of the same scene.  L = sum (s - s*)^2 +
+    sum (v - v*)^2 with fixed targets (not timed)."""
+    import torch
+
+    from paper_2210_06160_gb300 import rtsdf as rt
+    from paper_2210_06160_gb300 import scenes
+
+    ds = scenes.scene_diff()
+    sc = ds.scene
+    g = sc.grid
+    verts = torch.from_numpy(sc.verts).to(dev)
+    tris = torch.from_numpy(sc.tris).to(dev)
+    pts = torch.from_numpy(ds.pts).to(dev)
+    pos = torch.from_numpy(sc.recv_pos).to(dev)
+    nrm = torch.from_numpy(sc.recv_nrm).to(dev)
+    rp = rt.make_refine_params(sc.refine)
+    sp = rt.make_shadow_params(sc.shadow)
+    frames = [sc.refine]
+    plain = rt.Pipeline(g, len(sc.verts), len(sc.tris), device=dev)
+    tracked = rt.Pipeline(g, len(sc.verts), len(sc.tris), device=dev, track=True)
+    s_tgt = torch.zeros(len(ds.pts), dtype=torch.float32, device=dev)
+    v_tgt = torch.full((len(sc.recv_pos),), 0.5, dtype=torch.float32, device=dev)
+    light = torch.tensor(sc.shadow.light_dir, dtype=torch.float32, requires_grad=True)
+    stream = torch.cuda.current_stream()
+
+    def plain_fwd():
+        plain.rebuild(verts, tris, sc.jfa_steps, rp)
+        plain.sample(pts)
+        plain.shadow(pos, nrm, sp)
+
+    def fwd_bwd(ev=None):
+        v = verts.clone().requires_grad_(True)
+        if ev:
+            ev[0].record(stream)
+        samples, vis = rt.sdf_shadow(v, light, tracked, tris, sc.jfa_steps, frames, pts, pos, nrm, sc.shadow)
+        loss = ((samples - s_tgt) ** 2).sum() + ((vis - v_tgt) ** 2).sum()
+        if ev:
+            ev[1].record(stream)
+        loss.backward()
+        if ev:
+            ev[2].record(stream)
+        light.grad = None
+
+    for _ in range(warmup):
+        plain_fwd()
+        fwd_bwd()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    for _ in range(steps):
+        plain_fwd()
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e[0].elapsed_time(e[1]) / steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(steps):
+        fwd_bwd(evs[i])
+    torch.cuda.synchronize()
+    fwd_ms = statistics.mean(x[0].elapsed_time(x[1]) for x in evs)
+    bwd_ms = statistics.mean(x[1].elapsed_time(x[2]) for x in evs)
+    # the adjoint call alone (the state of the last forward is still in `tracked`)
+    d_verts = torch.empty_like(verts)
+    d_light = torch.empty(3, dtype=torch.float32, device=dev)
+    ws = torch.empty(rt.rtsdf_backward_workspace(tracked.g), dtype=torch.uint8, device=dev)
+    ds_ = torch.ones(len(ds.pts), dtype=torch.float32, device=dev)
+    dv_ = torch.ones(len(sc.recv_pos), dtype=torch.float32, device=dev)
+    sp_l = rt.make_shadow_params(sc.shadow)
+
+    def adj():
+        rt.rtsdf_backward(tracked.g, verts, tris, tracked.nearest, tracked.rep_tri, tracked.front, tracked.back,
+                          tracked.win_ray, tracked.win_tri, rp, tracked.sdf, pts, ds_, pos, nrm, sp_l, dv_, d_verts,
+                          d_light, ws)
+
+    for _ in range(warmup):
+        adj()
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(steps):
+        adj()
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    adj_ms = e[0].elapsed_time(e[1]) / steps
+    return {"workload": (f"differentiation {g.nx}^3, {len(sc.tris)} triangles (8 icospheres s3 + 2 boxes), "
+                         f"{len(ds.pts)} samples, {int(len(sc.recv_pos) ** 0.5)}^2 shadow, "
+                         f"{sc.refine.rays_per_voxel} rays/voxel"),
+            "plain_forward_ms": round(plain_ms, 4), "tracked_forward_ms": round(fwd_ms, 4),
+            "backward_ms": round(bwd_ms, 4), "rtsdf_backward_ms": round(adj_ms, 4),
+            "fwd_bwd_gvoxel_per_s": round(g.nvox / ((fwd_ms + bwd_ms) * 1e-3) / 1e9, 3),
+            "plain_gvoxel_per_s": round(g.nvox / (plain_ms * 1e-3) / 1e9, 3),
+            "fwd_bwd_vs_plain": round((fwd_ms + bwd_ms) / plain_ms, 3), "steps": steps}
+
 
 def run_ours(args):
     import numpy as np
@@ -337,6 +429,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h_verts.numel() * 4 + h_tris.numel() * 4),
                "d2h_bytes_per_step": int(h_sdf.numel() * 4 + h_vis.numel() * 4), "steps": ke}
 
+    bwd = None
+    if args.workload == "room" and not args.no_extensions:
+        bwd = bench_backward(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_frame_sample(sc)
@@ -350,6 +446,7 @@ def run_ours(args):
                 "rebuild_ms": round(rebuild_ms, 4),
                 "stage_ms": {k: round(v, 4) for k, v in stage.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "backward": bwd,
                 "clocks": clk, "counters": counters, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -192,6 +192,24 @@ rtsdf_status rtsdf_refine(const rtsdf_grid* g, const float* verts, int32_t V, co
                           uint32_t* front, uint32_t* back, float* sdf_out, void* ws, size_t ws_bytes,
                           rtsdf_counters* counters, rtsdf_stream stream);
 
+/* Refinement that also records, per voxel, the source that set its distance (the
+ * winner), for rtsdf_backward.  Arguments, outputs and errors are those of
+ * rtsdf_refine, plus two nx*ny*nz arrays (device, 16-byte aligned, both non-NULL):
+ *   win_ray[v] = ray id (frame_index*R + r) of the hit that set dist[v], or
+ *                0xFFFFFFFF when the coarse distance u_c holds it (always at
+ *                unmasked voxels);
+ *   win_tri[v] = that hit's triangle id, or -1.
+ * Among this call's rays the winner is the smallest (t, triangle id), the first
+ * ray on ties; it replaces the record only when it lowers dist.  With accumulate
+ * = 0 every record starts at the coarse source; with accumulate = 1 the coarse
+ * source takes over a voxel when u_c lowers its distance. */
+rtsdf_status rtsdf_refine_tracked(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris,
+                                  int32_t T, const void* bvh, size_t bvh_bytes, const int32_t* nearest,
+                                  const int32_t* rep_tri, const rtsdf_refine_params* p, uint32_t* dist_bits,
+                                  uint32_t* front, uint32_t* back, float* sdf_out, uint32_t* win_ray,
+                                  int32_t* win_tri, void* ws, size_t ws_bytes, rtsdf_counters* counters,
+                                  rtsdf_stream stream);
+
 /* ---------------------------------------------------------------- shadow */
 
 /* Sec. 2.4 sphere tracing toward a directional light with the penumbra estimate
@@ -204,6 +222,53 @@ rtsdf_status rtsdf_refine(const rtsdf_grid* g, const float* verts, int32_t V, co
  * vis[i] in [0, 1]. */
 rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm,
                           int32_t P, const rtsdf_shadow_params* p, float* vis, rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- field samples */
+
+/* The field at M world points pts[3m..] (voxel coordinates (p - origin)/h, then
+ * trilinear between voxel centres with clamp to edge, FP32 lerps in x, y, z: the
+ * sampling the shadow raymarch of Sec. 2.4 uses).  out: M floats (voxel units). */
+rtsdf_status rtsdf_sample(const rtsdf_grid* g, const float* sdf, const float* pts, int32_t M, float* out,
+                          rtsdf_stream stream);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/* Longest raymarch (rtsdf_shadow_params.steps) rtsdf_backward replays. */
+#define RTSDF_BACKWARD_MAX_STEPS 512
+
+size_t rtsdf_backward_workspace(const rtsdf_grid* g);
+
+/* No counterpart in the paper: the adjoint of the forward outputs
+ *   samples = rtsdf_sample(sdf, pts)            (M values)
+ *   vis     = rtsdf_shadow(sdf, pos, nrm, sp)   (P values)
+ * with respect to the mesh vertices (world units) and the light direction
+ * sp->light_dir (unnormalised, as passed), given upstream gradients d_samples (M)
+ * and d_vis (P).  The field is the one the forward built on this grid from
+ * verts/tris: nearest (flooded seeds), rep_tri (voxelizer), front/back (votes) and
+ * win_ray/win_tri (rtsdf_refine_tracked) after its last frame, with the refine
+ * parameters rp of that frame (mask, key, scene_id, sign_fallback; the voxel's ray
+ * id in win_ray already includes the frame).  Every discrete choice of the forward
+ * is held fixed: the representative triangle, the mask, the vote, the winning
+ * source, and the raymarch's control flow; the adjoint is the exact derivative of
+ * that frozen function:
+ *   coarse voxels (Sec. 2.2): d|q - p| / dX_m = lambda_m (q - p)/|q - p| (closest
+ *     point q with barycentric weights lambda);
+ *   refined voxels (Sec. 2.1): dt / dX_m = lambda_m n / (d . n) (hit t of the
+ *     winning ray d on its triangle, normal n, weights lambda of the hit point);
+ *   samples: trilinear weights; shadow (Sec. 2.4, 2.5.2): reverse mode through the
+ *     replayed march and the penumbra estimate at its minimising sample.
+ * Outputs (overwritten): d_verts [V][3], d_light [3], both device float.  The FP32
+ * sums are accumulated with atomics, so the last bits vary between runs.
+ * pts/d_samples may be NULL when M = 0, pos/nrm/d_vis when P = 0.
+ * sp->steps > RTSDF_BACKWARD_MAX_STEPS -> RTSDF_EINVAL.
+ * ws >= rtsdf_backward_workspace(g). */
+rtsdf_status rtsdf_backward(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                            const int32_t* nearest, const int32_t* rep_tri, const uint32_t* front,
+                            const uint32_t* back, const uint32_t* win_ray, const int32_t* win_tri,
+                            const rtsdf_refine_params* rp, const float* sdf, const float* pts, int32_t M,
+                            const float* d_samples, const float* pos, const float* nrm, int32_t P,
+                            const rtsdf_shadow_params* sp, const float* d_vis, float* d_verts, float* d_light,
+                            void* ws, size_t ws_bytes, rtsdf_stream stream);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -67,6 +67,7 @@ def lib():
                 "or_vote_sign": (C.c_int, [u32, u32, P, P, P, P, C.c_int]),
                 "or_finalize": (None, [G, P, P, P, P, P, P, P, P, P, f32, C.c_int, P]),
                 "or_trilinear": (f32, [G, P, f32, f32, f32]),
+                "or_sample": (None, [G, P, P, i32, P]),
                 "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P]),
                 "or_num_threads": (C.c_int, []),
                 "or_frozen_sources": (None, [G, P, P, P, P, P, P, P, P, P, P, u32, C.c_int, P]),
@@ -147,6 +148,14 @@ def ray_tri(o, d, a, b, c, tmax: float):
     f = np.zeros(1, dtype=np.int32)
     hit = lib().or_ray_tri(_p(o), _p(d), _p(a), _p(b), _p(c), float(tmax), _p(t), _p(f))
     return (bool(hit), float(t[0]), bool(f[0])) if hit else (False, None, None)
+
+
+def sample(grid, sdf, pts) -> np.ndarray:
+    """The FP32 field at world points (trilinear, clamp to edge)."""
+    s, pts = _f32(sdf), _f32(pts)
+    out = np.empty(len(pts), dtype=np.float32)
+    lib().or_sample(C.byref(_g(grid)), _p(s), _p(pts), len(pts), _p(out))
+    return out
 
 
 def trilinear(grid, sdf, q) -> float:

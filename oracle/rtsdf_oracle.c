@@ -511,6 +511,13 @@ float or_trilinear(const or_grid* g, const float* sdf, float qx, float qy, float
     return lerpf(c0, c1, f[2]);
 }
 
+void or_sample(const or_grid* g, const float* sdf, const float* pts, int32_t M, float* out) {
+    for (int32_t m = 0; m < M; ++m) {
+        const float* p = pts + 3 * (int64_t)m;
+        out[m] = or_trilinear(g, sdf, (p[0] - g->ox) / g->h, (p[1] - g->oy) / g->h, (p[2] - g->oz) / g->h);
+    }
+}
+
 /* Sphere tracing toward the light (Sec. 2.4) with the penumbra estimate
  * k * (closest approach) / (distance along the ray), where the closest approach
  * between two successive samples is triangulated from the two sampled distances

@@ -103,6 +103,9 @@ void or_finalize(const or_grid* g, const float* vv, const int32_t* tris, const i
 /* Trilinear sample of a voxel-centred grid at voxel coordinate q (clamp to edge). */
 float or_trilinear(const or_grid* g, const float* sdf, float qx, float qy, float qz);
 
+/* The field at M world points: q = (p - o) / h per component, then trilinear. */
+void or_sample(const or_grid* g, const float* sdf, const float* pts, int32_t M, float* out);
+
 /* Sec. 2.4 / 2.5.2: soft-shadow visibility of P receivers (world positions and
  * unit normals) toward a directional light, sphere tracing the SDF (voxel units). */
 void or_shadow(const or_grid* g, const float* sdf, const float* pos, const float* nrm, int32_t P,

@@ -296,6 +296,7 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
         int cells[OR_MAX_STEPS][3];
         unsigned char capped[OR_MAX_STEPS];
         int nsteps = 0, argmin = -1, hit = 0;
+        int den_tiny32 = 0, e_pos32 = 0; /* branches of the estimate at the argmin */
         for (int32_t s = 0; s < ns; ++s) {
             const float q[3] = {org32[0] + t32 * L32[0], org32[1] + t32 * L32[1], org32[2] + t32 * L32[2]};
             if (q[0] < 0.0f || q[0] > nxf || q[1] < 0.0f || q[1] > nyf || q[2] < 0.0f || q[2] > nzf) break;
@@ -313,6 +314,8 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
             if (r < res32) {
                 res32 = r;
                 argmin = s;
+                den_tiny32 = !(t32 - y > 1e-6f);
+                e_pos32 = dd - y * y > 0.0f;
             }
             dprev32 = d;
             capped[s] = !(d < max_step);
@@ -320,8 +323,9 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
         }
         /* --- FP64 values along the frozen path */
         const double tg = (double)target[pi];
-        if (hit || argmin < 0 || res32 <= 0.0f) {
-            const double v = hit ? 0.0 : (res32 <= 0.0f ? 0.0 : 1.0);
+        if (hit || argmin < 0 || !(res32 > 0.0f) || !(res32 < 1.0f)) {
+            /* the clamped output is constant on the frozen path */
+            const double v = (hit || !(res32 > 0.0f)) ? 0.0 : 1.0;
             loss += (v - tg) * (v - tg);
             continue;
         }
@@ -341,15 +345,13 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
         const double d = dv[i], dp = i > 0 ? dv[i - 1] : INFINITY;
         const double y = i > 0 ? d * d / (2 * dp) : 0.0;
         const double e2 = d * d - y * y;
-        const double e = e2 > 0 ? sqrt(e2) : 0.0;
-        const double den_raw = tt[i] - y;
-        const int den_tiny = !(den_raw > 1e-6);
-        const double den = den_tiny ? 1e-6 : den_raw;
+        const double e = e_pos32 && e2 > 0 ? sqrt(e2) : 0.0;
+        const int den_tiny = den_tiny32;
+        const double den = den_tiny ? 1e-6 : tt[i] - y;
         const double res = k * e / den;
-        const double vis = res < 1.0 ? res : 1.0;
+        const double vis = res;
         loss += (vis - tg) * (vis - tg);
         if (!gsdf && !gl) continue;
-        if (!(res < 1.0)) continue;
         /* --- reverse mode along the frozen path */
         const double gr = 2 * (vis - tg);
         double gd[OR_MAX_STEPS], gt[OR_MAX_STEPS + 1];

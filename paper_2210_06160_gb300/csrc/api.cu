@@ -93,10 +93,13 @@ rtsdf_status rtsdf_jfa(const rtsdf_grid* g, int32_t* buf_a, int32_t* buf_b, cons
 
 size_t rtsdf_refine_workspace(const rtsdf_grid* g) { return grid_ok(g) ? refine_workspace(*g) : 0; }
 
-rtsdf_status rtsdf_refine(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
-                          const void* bvh, size_t bvh_bytes_, const int32_t* nearest, const int32_t* rep_tri,
-                          const rtsdf_refine_params* p, uint32_t* dist_bits, uint32_t* front, uint32_t* back,
-                          float* sdf_out, void* ws, size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream) {
+namespace {
+
+rtsdf_status refine_checked(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                            const void* bvh, size_t bvh_bytes_, const int32_t* nearest, const int32_t* rep_tri,
+                            const rtsdf_refine_params* p, uint32_t* dist_bits, uint32_t* front, uint32_t* back,
+                            float* sdf_out, uint32_t* win_ray, int32_t* win_tri, void* ws, size_t ws_bytes,
+                            rtsdf_counters* counters, rtsdf_stream stream) {
     if (!grid_ok(g) || !mesh_ok(verts, V, tris, T) || !p) return RTSDF_EINVAL;
     if (!buf_ok(bvh, 256) || !buf_ok(nearest, 16) || !buf_ok(rep_tri, 16) || !buf_ok(dist_bits, 16) ||
         !buf_ok(front, 16) || !buf_ok(back, 16) || !buf_ok(sdf_out, 16) || !buf_ok(ws, 256))
@@ -108,18 +111,78 @@ rtsdf_status rtsdf_refine(const rtsdf_grid* g, const float* verts, int32_t V, co
     if (bvh_bytes_ < bvh_bytes(T)) return RTSDF_ENOMEM;
     if (ws_bytes < refine_workspace(*g)) return RTSDF_ENOMEM;
     return refine(*g, verts, V, tris, T, bvh, nearest, rep_tri, *p, dist_bits, front, back, sdf_out, ws, counters,
-                  cs(stream));
+                  win_ray, win_tri, cs(stream));
+}
+
+bool refine_params_ok(const rtsdf_refine_params* p) {
+    return p && p->rays_per_voxel >= 1 && p->rays_per_voxel <= 4096 && p->mask_vox >= 0.0f &&
+           isfinite(p->mask_vox) && isfinite(p->beta_vox);
+}
+
+bool shadow_params_ok(const rtsdf_shadow_params* p) {
+    if (!p) return false;
+    const float* l = p->light_dir;
+    const float len2 = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
+    return len2 > 0.0f && isfinite(len2) && p->steps >= 0 && p->max_step_vox > 0.0f && isfinite(p->k);
+}
+
+}  // namespace
+
+rtsdf_status rtsdf_refine(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                          const void* bvh, size_t bvh_bytes_, const int32_t* nearest, const int32_t* rep_tri,
+                          const rtsdf_refine_params* p, uint32_t* dist_bits, uint32_t* front, uint32_t* back,
+                          float* sdf_out, void* ws, size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream) {
+    return refine_checked(g, verts, V, tris, T, bvh, bvh_bytes_, nearest, rep_tri, p, dist_bits, front, back, sdf_out,
+                          nullptr, nullptr, ws, ws_bytes, counters, stream);
+}
+
+rtsdf_status rtsdf_refine_tracked(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                                  const void* bvh, size_t bvh_bytes_, const int32_t* nearest, const int32_t* rep_tri,
+                                  const rtsdf_refine_params* p, uint32_t* dist_bits, uint32_t* front, uint32_t* back,
+                                  float* sdf_out, uint32_t* win_ray, int32_t* win_tri, void* ws, size_t ws_bytes,
+                                  rtsdf_counters* counters, rtsdf_stream stream) {
+    if (!buf_ok(win_ray, 16) || !buf_ok(win_tri, 16)) return RTSDF_EINVAL;
+    return refine_checked(g, verts, V, tris, T, bvh, bvh_bytes_, nearest, rep_tri, p, dist_bits, front, back, sdf_out,
+                          win_ray, win_tri, ws, ws_bytes, counters, stream);
 }
 
 rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm, int32_t P,
                           const rtsdf_shadow_params* p, float* vis, rtsdf_stream stream) {
     if (!grid_ok(g) || !p || P < 0 || !buf_ok(sdf, 16)) return RTSDF_EINVAL;
     if (P > 0 && (!buf_ok(pos, 4) || !buf_ok(nrm, 4) || !buf_ok(vis, 4))) return RTSDF_EINVAL;
-    const float* l = p->light_dir;
-    const float len2 = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
-    if (!(len2 > 0.0f) || !isfinite(len2) || p->steps < 0 || !(p->max_step_vox > 0.0f) || !isfinite(p->k))
-        return RTSDF_EINVAL;
+    if (!shadow_params_ok(p)) return RTSDF_EINVAL;
     return shadow(*g, sdf, pos, nrm, P, *p, vis, cs(stream));
+}
+
+rtsdf_status rtsdf_sample(const rtsdf_grid* g, const float* sdf, const float* pts, int32_t M, float* out,
+                          rtsdf_stream stream) {
+    if (!grid_ok(g) || M < 0 || !buf_ok(sdf, 16)) return RTSDF_EINVAL;
+    if (M > 0 && (!buf_ok(pts, 4) || !buf_ok(out, 4))) return RTSDF_EINVAL;
+    return sample(*g, sdf, pts, M, out, cs(stream));
+}
+
+size_t rtsdf_backward_workspace(const rtsdf_grid* g) { return grid_ok(g) ? backward_workspace(*g) : 0; }
+
+rtsdf_status rtsdf_backward(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
+                            const int32_t* nearest, const int32_t* rep_tri, const uint32_t* front,
+                            const uint32_t* back, const uint32_t* win_ray, const int32_t* win_tri,
+                            const rtsdf_refine_params* rp, const float* sdf, const float* pts, int32_t M,
+                            const float* d_samples, const float* pos, const float* nrm, int32_t P,
+                            const rtsdf_shadow_params* sp, const float* d_vis, float* d_verts, float* d_light,
+                            void* ws, size_t ws_bytes, rtsdf_stream stream) {
+    if (!grid_ok(g) || !mesh_ok(verts, V, tris, T) || !refine_params_ok(rp) || !shadow_params_ok(sp))
+        return RTSDF_EINVAL;
+    if (sp->steps > RTSDF_BACKWARD_MAX_STEPS || M < 0 || P < 0) return RTSDF_EINVAL;
+    if (!buf_ok(nearest, 16) || !buf_ok(rep_tri, 16) || !buf_ok(front, 16) || !buf_ok(back, 16) ||
+        !buf_ok(win_ray, 16) || !buf_ok(win_tri, 16) || !buf_ok(sdf, 16) || !buf_ok(d_light, 4) ||
+        !buf_ok(ws, 256))
+        return RTSDF_EINVAL;
+    if (V > 0 && !buf_ok(d_verts, 4)) return RTSDF_EINVAL;
+    if (M > 0 && (!buf_ok(pts, 4) || !buf_ok(d_samples, 4))) return RTSDF_EINVAL;
+    if (P > 0 && (!buf_ok(pos, 4) || !buf_ok(nrm, 4) || !buf_ok(d_vis, 4))) return RTSDF_EINVAL;
+    if (ws_bytes < backward_workspace(*g)) return RTSDF_ENOMEM;
+    return backward(*g, verts, V, tris, T, nearest, rep_tri, front, back, win_ray, win_tri, *rp, sdf, pts, M,
+                    d_samples, pos, nrm, P, *sp, d_vis, d_verts, d_light, ws, cs(stream));
 }
 
 }  // extern "C"

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __
                                                  uint32_t* __restrict__ dist_bits, uint32_t* __restrict__ front,
                                                  uint32_t* __restrict__ back, float* __restrict__ sdf,
                                                  unsigned long long* __restrict__ bmask,
-                                                 int32_t* __restrict__ blist, uint32_t* __restrict__ count) {
+                                                 int32_t* __restrict__ blist, uint32_t* __restrict__ count,
+                                                 uint32_t* __restrict__ win_ray, int32_t* __restrict__ win_tri) {
     __shared__ unsigned long long smask[8];
     const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz = threadIdx.x >> 7;
     const int i = blockIdx.x * 32 + tx, j = blockIdx.y * kB + ty, k = blockIdx.z * kB + tz;
@@ -111,17 +112,26 @@ __global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __
             const int dx = i - si, dy = j - sj, dz = k - sk;
             masked = (float)(dx * dx + dy * dy + dz * dz) <= a.mask2;
         }
+        // winner record (tracked calls): the coarse source holds a voxel's distance
+        // when the voxel is unmasked, starts fresh, or its coarse distance is lower
+        bool coarse_wins = true;
         if (!masked) {
             sdf[lin] = uc - a.beta;
         } else {
             const uint32_t ub = __float_as_uint(uc);
             if (a.accumulate) {
-                dist_bits[lin] = min(dist_bits[lin], ub);
+                const uint32_t old = dist_bits[lin];
+                coarse_wins = ub < old;
+                dist_bits[lin] = min(old, ub);
             } else {
                 dist_bits[lin] = ub;
                 front[lin] = 0u;
                 back[lin] = 0u;
             }
+        }
+        if (win_ray && coarse_wins) {
+            win_ray[lin] = 0xFFFFFFFFu;
+            win_tri[lin] = -1;
         }
     }
     const uint32_t bal = __ballot_sync(0xffffffffu, masked);
@@ -301,6 +311,7 @@ __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf
 // not diverge.  Both filters are conservative (their margins exceed FP32 rounding
 // of the exact test), so they never drop a triangle the exact test accepts; they
 // may use fused multiply-adds because they decide nothing the oracle decides.
+template <bool kTrack>
 __global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
@@ -312,7 +323,9 @@ __global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, cons
                                                               uint32_t* __restrict__ dist_bits,
                                                               uint32_t* __restrict__ front,
                                                               uint32_t* __restrict__ back, float* __restrict__ sdf,
-                                                              rtsdf_counters* counters) {
+                                                              rtsdf_counters* counters,
+                                                              uint32_t* __restrict__ win_ray,
+                                                              int32_t* __restrict__ win_tri) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
@@ -321,7 +334,6 @@ __global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, cons
     const uint32_t nact = count[0];
     uint32_t n_hit = 0, n_fail = 0, n_ovf = 0;
     const float ext = a.tmax * 1.00001f + 1e-3f;
-    const uint32_t lt_mask = (1u << lane) - 1u;
 
     while (true) {
         uint32_t wk = 0;
@@ -370,6 +382,9 @@ __global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, cons
             }
             w.origin[lane] = make_float4(o.x, o.y, o.z, 0.f);
             uint32_t vbest = 0xffffffffu, vfront = 0, vback = 0;
+            // tracked: this call's winning ray, ordered by (t, triangle id), first ray on ties
+            unsigned long long wkey = ~0ull;
+            uint32_t wray = 0xFFFFFFFFu;
             for (int r0 = 0; r0 < a.R; r0 += kRaysPerLane) {
                 float3 dir[kRaysPerLane];
                 uint32_t okm = 0;
@@ -454,12 +469,21 @@ __global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, cons
                         vbest = min(vbest, (uint32_t)(key >> 32));
                         if (key & 1ull) ++vfront; else ++vback;
                         ++n_hit;
+                        if (kTrack && (key >> 1) < wkey) {
+                            wkey = key >> 1;
+                            wray = a.frame * (uint32_t)a.R + (uint32_t)(r0 + r);
+                        }
                     }
                 }
                 __syncwarp();
             }
             if (mine) {
-                const uint32_t d = min(dist_bits[lin], vbest);
+                const uint32_t old = dist_bits[lin];
+                const uint32_t d = min(old, vbest);
+                if (kTrack && vbest < old) {
+                    win_ray[lin] = wray;
+                    win_tri[lin] = (int32_t)(wkey & 0x7FFFFFFFull);
+                }
                 const uint32_t fr = front[lin] + vfront, bk = back[lin] + vback;
                 dist_bits[lin] = d;
                 front[lin] = fr;
@@ -502,7 +526,7 @@ __global__ void k_refine_report(const uint32_t* __restrict__ count, const unsign
 rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const int32_t* tris, int32_t T,
                     const void* bvh, const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params& p,
                     uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf, void* ws,
-                    rtsdf_counters* counters, cudaStream_t s) {
+                    rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, cudaStream_t s) {
     RefineArgs a;
     a.g = to_dev(gh);
     a.verts = verts;
@@ -529,18 +553,27 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
     const auto* leaves = reinterpret_cast<const BvhLeaf*>(static_cast<const char*>(bvh) + bvh_leaves_offset(T));
     RTSDF_CUDA(cudaMemsetAsync(w.count, 0, 16, s));
     const dim3 rgrid((gh.nx + 31) / 32, a.nby, a.nbz);
-    k_resolve<<<rgrid, 512, 0, s>>>(a, nearest, rep_tri, dist_bits, front, back, sdf, w.bmask, w.blist, w.count);
+    const bool track = win_ray != nullptr;
+    k_resolve<<<rgrid, 512, 0, s>>>(a, nearest, rep_tri, dist_bits, front, back, sdf, w.bmask, w.blist, w.count,
+                                    track ? win_ray : nullptr, track ? win_tri : nullptr);
     RTSDF_LAUNCHED();
     const size_t smem = sizeof(WarpSmem) * (kRefineThreads / 32);
-    static bool attr_set[64] = {false};
+    static bool attr_set[64][2] = {};
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RTSDF_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set[dev] = true;
+    if (dev >= 0 && dev < 64 && !attr_set[dev][track]) {
+        RTSDF_CUDA(cudaFuncSetAttribute(track ? k_refine<true> : k_refine<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[dev][track] = true;
     }
-    k_refine<<<num_sms() * 8, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
-                                                       w.count, dist_bits, front, back, sdf, counters);
+    if (track)
+        k_refine<true><<<num_sms() * 8, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
+                                                                 w.blist, w.count, dist_bits, front, back, sdf,
+                                                                 counters, win_ray, win_tri);
+    else
+        k_refine<false><<<num_sms() * 8, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
+                                                                  w.blist, w.count, dist_bits, front, back, sdf,
+                                                                  counters, nullptr, nullptr);
     RTSDF_LAUNCHED();
     if (counters) {
         k_refine_report<<<num_sms(), 256, 0, s>>>(w.count, w.bmask, nbricks(gh), counters);

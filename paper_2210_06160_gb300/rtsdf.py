@@ -69,8 +69,17 @@ _SIGS = {
     "rtsdf_refine_workspace": (C.c_size_t, [C.POINTER(Grid)]),
     "rtsdf_refine": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t, _P, _P,
                                C.POINTER(RefineParams), _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
+    "rtsdf_refine_tracked": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t, _P, _P,
+                                       C.POINTER(RefineParams), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
     "rtsdf_shadow": (C.c_int, [C.POINTER(Grid), _P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P]),
+    "rtsdf_sample": (C.c_int, [C.POINTER(Grid), _P, _P, C.c_int32, _P, _P]),
+    "rtsdf_backward_workspace": (C.c_size_t, [C.POINTER(Grid)]),
+    "rtsdf_backward": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P,
+                                 C.POINTER(RefineParams), _P, _P, C.c_int32, _P, _P, _P, C.c_int32,
+                                 C.POINTER(ShadowParams), _P, _P, _P, _P, C.c_size_t, _P]),
 }
+
+BACKWARD_MAX_STEPS = 512
 
 
 def lib() -> C.CDLL:
@@ -147,6 +156,10 @@ def rtsdf_refine_workspace(grid: Grid) -> int:
     return int(lib().rtsdf_refine_workspace(C.byref(grid)))
 
 
+def rtsdf_backward_workspace(grid: Grid) -> int:
+    return int(lib().rtsdf_backward_workspace(C.byref(grid)))
+
+
 # ------------------------------------------------------------ the calls
 
 def rtsdf_voxelize(verts, tris, grid: Grid, seed, rep_tri, ws, counters=None, stream=None) -> None:
@@ -195,6 +208,43 @@ def rtsdf_refine(grid: Grid, verts, tris, bvh, nearest, rep_tri, params: RefineP
                               _stream(stream)), "rtsdf_refine")
 
 
+def rtsdf_refine_tracked(grid: Grid, verts, tris, bvh, nearest, rep_tri, params: RefineParams, dist_bits, front,
+                         back, sdf_out, win_ray, win_tri, ws, counters=None, stream=None) -> None:
+    """rtsdf_refine that also records the winning source of every voxel's distance."""
+    _check(lib().rtsdf_refine_tracked(C.byref(grid), _dev(verts, torch.float32, "verts"), verts.shape[0],
+                                      _dev(tris, torch.int32, "tris"), tris.shape[0], _dev(bvh, torch.uint8, "bvh"),
+                                      bvh.numel(), _dev(nearest, torch.int32, "nearest"),
+                                      _dev(rep_tri, torch.int32, "rep_tri"), C.byref(params),
+                                      _dev(dist_bits, torch.int32, "dist_bits"), _dev(front, torch.int32, "front"),
+                                      _dev(back, torch.int32, "back"), _dev(sdf_out, torch.float32, "sdf_out"),
+                                      _dev(win_ray, torch.int32, "win_ray"), _dev(win_tri, torch.int32, "win_tri"),
+                                      _dev(ws, torch.uint8, "ws"), ws.numel(), _dev(counters, torch.int32, "counters"),
+                                      _stream(stream)), "rtsdf_refine_tracked")
+
+
+def rtsdf_sample(grid: Grid, sdf, pts, out, stream=None) -> None:
+    _check(lib().rtsdf_sample(C.byref(grid), _dev(sdf, torch.float32, "sdf"), _dev(pts, torch.float32, "pts"),
+                              pts.shape[0], _dev(out, torch.float32, "out"), _stream(stream)), "rtsdf_sample")
+
+
+def rtsdf_backward(grid: Grid, verts, tris, nearest, rep_tri, front, back, win_ray, win_tri, rparams: RefineParams,
+                   sdf, pts, d_samples, pos, nrm, sparams: ShadowParams, d_vis, d_verts, d_light, ws,
+                   stream=None) -> None:
+    M = 0 if pts is None else pts.shape[0]
+    P = 0 if pos is None else pos.shape[0]
+    _check(lib().rtsdf_backward(C.byref(grid), _dev(verts, torch.float32, "verts"), verts.shape[0],
+                                _dev(tris, torch.int32, "tris"), tris.shape[0],
+                                _dev(nearest, torch.int32, "nearest"), _dev(rep_tri, torch.int32, "rep_tri"),
+                                _dev(front, torch.int32, "front"), _dev(back, torch.int32, "back"),
+                                _dev(win_ray, torch.int32, "win_ray"), _dev(win_tri, torch.int32, "win_tri"),
+                                C.byref(rparams), _dev(sdf, torch.float32, "sdf"),
+                                _dev(pts, torch.float32, "pts"), M, _dev(d_samples, torch.float32, "d_samples"),
+                                _dev(pos, torch.float32, "pos"), _dev(nrm, torch.float32, "nrm"), P,
+                                C.byref(sparams), _dev(d_vis, torch.float32, "d_vis"),
+                                _dev(d_verts, torch.float32, "d_verts"), _dev(d_light, torch.float32, "d_light"),
+                                _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)), "rtsdf_backward")
+
+
 def rtsdf_shadow(grid: Grid, sdf, pos, nrm, params: ShadowParams, vis, stream=None) -> None:
     _check(lib().rtsdf_shadow(C.byref(grid), _dev(sdf, torch.float32, "sdf"), _dev(pos, torch.float32, "pos"),
                               _dev(nrm, torch.float32, "nrm"), pos.shape[0], C.byref(params),
@@ -219,7 +269,7 @@ class Pipeline:
     uint32 state (dist_bits, front, back) is held in int32 tensors of the same bits.
     """
 
-    def __init__(self, grid, n_verts: int, n_tris: int, device="cuda"):
+    def __init__(self, grid, n_verts: int, n_tris: int, device="cuda", track: bool = False):
         self.g = make_grid(grid)
         self.T, self.V = int(n_tris), int(n_verts)
         dev = torch.device(device)
@@ -241,6 +291,11 @@ class Pipeline:
         self.ws_bvh = torch.empty(rtsdf_bvh_workspace(self.T), **u8)
         self.ws_refine = torch.empty(rtsdf_refine_workspace(self.g), **u8)
         self.nearest = None
+        # winner record for the adjoint (rtsdf_refine_tracked)
+        self.track = bool(track)
+        self.win_ray = torch.empty(shp, **i32) if track else None
+        self.win_tri = torch.empty(shp, **i32) if track else None
+        self.generation = 0  # bumped by every call that changes the field
 
     def voxelize(self, verts, tris, stream=None):
         rtsdf_voxelize(verts, tris, self.g, self.buf_a, self.rep_tri, self.ws_vox, self.counters, stream)
@@ -254,8 +309,14 @@ class Pipeline:
         return self.nearest
 
     def refine(self, verts, tris, params: RefineParams, stream=None):
-        rtsdf_refine(self.g, verts, tris, self.bvh, self.nearest, self.rep_tri, params, self.dist_bits, self.front,
-                     self.back, self.sdf, self.ws_refine, self.counters, stream)
+        self.generation += 1
+        if self.track:
+            rtsdf_refine_tracked(self.g, verts, tris, self.bvh, self.nearest, self.rep_tri, params, self.dist_bits,
+                                 self.front, self.back, self.sdf, self.win_ray, self.win_tri, self.ws_refine,
+                                 self.counters, stream)
+        else:
+            rtsdf_refine(self.g, verts, tris, self.bvh, self.nearest, self.rep_tri, params, self.dist_bits,
+                         self.front, self.back, self.sdf, self.ws_refine, self.counters, stream)
         return self.sdf
 
     def rebuild(self, verts, tris, steps, params: RefineParams, stream=None):
@@ -269,3 +330,72 @@ class Pipeline:
             vis = torch.empty(pos.shape[0], dtype=torch.float32, device=pos.device)
         rtsdf_shadow(self.g, self.sdf, pos, nrm, params, vis, stream)
         return vis
+
+    def sample(self, pts, out=None, stream=None):
+        if out is None:
+            out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+        rtsdf_sample(self.g, self.sdf, pts, out, stream)
+        return out
+
+
+# ------------------------------------------------------------ differentiation
+
+class SDFShadow(torch.autograd.Function):
+    """(samples, vis) = field samples at `pts` and soft-shadow visibility of the
+    receivers, for a mesh whose field is rebuilt on `pipe` (voxelize, BVH, jump
+    flood, then one tracked refine per entry of `frames`); differentiable in the
+    vertices and the light direction through rtsdf_backward.
+
+    verts: CUDA float32 [V,3] world positions; light: float32 [3] tensor (any
+    device; its value parameterises the raymarch launch).  The backward must run
+    before `pipe` builds another field.
+    """
+
+    @staticmethod
+    def forward(ctx, verts, light, pipe, tris, jfa_steps, frames, pts, pos, nrm, shadow):
+        if not pipe.track:
+            raise RtsdfError("SDFShadow needs a Pipeline created with track=True")
+        if int(shadow.steps) > BACKWARD_MAX_STEPS:
+            raise RtsdfError(f"the adjoint replays at most {BACKWARD_MAX_STEPS} raymarch steps")
+        import dataclasses
+        sp = dataclasses.replace(shadow, light_dir=tuple(float(v) for v in light.detach().cpu().tolist()))
+        verts_c = verts.detach().contiguous()
+        pipe.voxelize(verts_c, tris)
+        pipe.build_bvh(verts_c, tris)
+        pipe.jfa(jfa_steps)
+        rparams = None
+        for rp in frames:
+            rparams = make_refine_params(rp)
+            pipe.refine(verts_c, tris, rparams)
+        samples = pipe.sample(pts)
+        vis = pipe.shadow(pos, nrm, make_shadow_params(sp))
+        ctx.pipe, ctx.gen = pipe, pipe.generation
+        ctx.rparams, ctx.sparams = rparams, make_shadow_params(sp)
+        ctx.tris, ctx.pts, ctx.pos, ctx.nrm = tris, pts, pos, nrm
+        ctx.light_device = light.device
+        ctx.save_for_backward(verts_c)
+        return samples, vis
+
+    @staticmethod
+    def backward(ctx, d_samples, d_vis):
+        (verts,) = ctx.saved_tensors
+        pipe = ctx.pipe
+        if pipe.generation != ctx.gen:
+            raise RtsdfError("the pipeline built another field since this forward; its adjoint is gone")
+        dev = verts.device
+        ds = torch.zeros(ctx.pts.shape[0], dtype=torch.float32, device=dev) if d_samples is None \
+            else d_samples.to(torch.float32).contiguous()
+        dv = torch.zeros(ctx.pos.shape[0], dtype=torch.float32, device=dev) if d_vis is None \
+            else d_vis.to(torch.float32).contiguous()
+        d_verts = torch.empty_like(verts)
+        d_light = torch.empty(3, dtype=torch.float32, device=dev)
+        ws = torch.empty(rtsdf_backward_workspace(pipe.g), dtype=torch.uint8, device=dev)
+        rtsdf_backward(pipe.g, verts, ctx.tris, pipe.nearest, pipe.rep_tri, pipe.front, pipe.back, pipe.win_ray,
+                       pipe.win_tri, ctx.rparams, pipe.sdf, ctx.pts, ds, ctx.pos, ctx.nrm, ctx.sparams, dv,
+                       d_verts, d_light, ws)
+        return (d_verts, d_light.to(ctx.light_device), None, None, None, None, None, None, None, None)
+
+
+def sdf_shadow(verts, light, pipe, tris, jfa_steps, frames, pts, pos, nrm, shadow):
+    """Differentiable field samples and shadow image (see SDFShadow)."""
+    return SDFShadow.apply(verts, light, pipe, tris, jfa_steps, frames, pts, pos, nrm, shadow)

@@ -322,3 +322,41 @@ def scene_small_room(seed: int = 7, n: int = 48, n_prims: int = 6) -> Scene:
                               accumulate=True, key=(0x12345678, 0x9abcdef0)),
                  ShadowParams(steps=96, max_step_vox=0.05 / h),
                  jfa_steps(g, extra_one=True), 2, pos, nrm)
+
+
+@dataclasses.dataclass
+class DiffScene:
+    """A scene for the adjoint: the forward's inputs plus the loss's sample points
+    and the vertices of the target copy (Gaussian-perturbed)."""
+    scene: Scene
+    pts: np.ndarray           # float32 [M,3] world sample points
+    verts_target: np.ndarray  # float32 [V,3]
+
+
+def scene_diff(n: int = 128, subdiv: int = 3, n_spheres: int = 8, n_boxes: int = 2, seed: int = 1010,
+               n_samples: int = 65_536, shadow_res: int = 512, noise: float = 0.01) -> DiffScene:
+    """Unit cube, n^3 grid; icospheres (radius 0.08-0.15) and boxes (half-extent
+    0.05-0.12, random rotation) at seeded positions; uniform sample points; a
+    receiver plane at y = 0.05 under them; the target copy has every vertex moved
+    by N(0, noise^2) per coordinate."""
+    rng = np.random.default_rng(seed)
+    Vs, Ts = icosphere(subdiv)
+    parts = []
+    for _ in range(n_spheres):
+        c = rng.uniform(0.2, 0.8, size=3)
+        parts.append((Vs * rng.uniform(0.08, 0.15) + c, Ts))
+    Vb, Tb = box_mesh()
+    for _ in range(n_boxes):
+        c = rng.uniform(0.25, 0.75, size=3)
+        parts.append(((Vb * rng.uniform(0.05, 0.12)) @ random_rotation(rng).T + c, Tb))
+    V, T = merge(parts)
+    V = V.astype(np.float32)
+    g = Grid(n, n, n, (0.0, 0.0, 0.0), 1.0 / n)
+    pos, nrm = receivers_plane(0.05, 0.0, 1.0, 0.0, 1.0, shadow_res, shadow_res)
+    sc = Scene(f"diff-{n}^3", V, T, g,
+               RefineParams(mask_vox=3.0, rays_per_voxel=8, max_ray_vox=8.0, beta_vox=1.0, key=(0x2210, 0x6160)),
+               ShadowParams(steps=64, max_step_vox=0.05 / g.h),
+               jfa_steps(g), 1, pos, nrm)
+    pts = rng.uniform(0.0, 1.0, size=(n_samples, 3)).astype(np.float32)
+    vt = (V + rng.normal(0.0, noise, size=V.shape)).astype(np.float32)
+    return DiffScene(sc, pts, vt)

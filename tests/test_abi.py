@@ -106,6 +106,38 @@ def test_refine_and_shadow_parameter_validation(lib):
     assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
 
 
+def test_adjoint_entry_validation(lib):
+    from paper_2210_06160_gb300.rtsdf import RefineParams, ShadowParams
+    g = _grid()
+    P = C.c_void_p
+    rp = RefineParams(3.0, 8, 8.0, 1.0)
+    ws = lib.rtsdf_backward_workspace(C.byref(g))
+    assert ws >= 4 * 8 * 8 * 8
+    refine_ws = lib.rtsdf_refine_workspace(C.byref(g))
+    bvh = lib.rtsdf_bvh_bytes(1)
+    # tracked refine: the winner arrays are required
+    assert lib.rtsdf_refine_tracked(C.byref(g), P(FAKE), 3, P(FAKE), 1, P(FAKE), bvh, P(FAKE), P(FAKE),
+                                    C.byref(rp), P(FAKE), P(FAKE), P(FAKE), P(FAKE), None, P(FAKE), P(FAKE),
+                                    refine_ws, None, None) == 1
+    # samples: negative count, misaligned field
+    assert lib.rtsdf_sample(C.byref(g), P(FAKE), P(FAKE), -1, P(FAKE), None) == 1
+    assert lib.rtsdf_sample(C.byref(g), P(FAKE + 4), P(FAKE), 4, P(FAKE), None) == 1
+    assert lib.rtsdf_sample(C.byref(g), P(FAKE), None, 0, None, None) == 0   # nothing to do
+
+    def bwd(sp, ws_bytes, M=4, Pn=4, win=P(FAKE)):
+        return lib.rtsdf_backward(C.byref(g), P(FAKE), 3, P(FAKE), 1, P(FAKE), P(FAKE), P(FAKE), P(FAKE), win,
+                                  P(FAKE), C.byref(rp), P(FAKE), P(FAKE), M, P(FAKE), P(FAKE), P(FAKE), Pn,
+                                  C.byref(sp), P(FAKE), P(FAKE), P(FAKE), P(FAKE), ws_bytes, None)
+
+    long_march = ShadowParams((C.c_float * 3)(0, 1, 0), 8.0, 513, 1.0)
+    assert bwd(long_march, ws) == 1
+    sp = ShadowParams((C.c_float * 3)(0, 1, 0), 8.0, 512, 1.0)
+    assert bwd(sp, ws - 1) == 2
+    assert bwd(sp, ws, win=None) == 1
+    assert bwd(sp, ws, M=-1) == 1
+    assert bwd(ShadowParams((C.c_float * 3)(0, 0, 0), 8.0, 64, 1.0), ws) == 1
+
+
 def test_product_path_has_no_cpu_fallback():
     """The binding raises when the compiled library is absent instead of computing
     anything itself, and nothing in the package imports the oracle."""
