@@ -187,6 +187,75 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU path
 
+def bench_batch(dev, steps: int = 5, warmup: int = 2) -> dict:
+    """48 seeded scenes of uneven sizes (dims from 32^3 .. 256x128x256, 500-60k
+    triangles, 8 rays/voxel): one batched rebuild (voxelize + BVH + JFA + refine,
+    autotuned refine shape, JFA chain from a CUDA graph) against 48 sequential
+    single-scene rebuilds on the same GPU."""
+    import torch
+
+    from paper_2210_06160_gb300 import rtsdf as rt
+    from paper_2210_06160_gb300 import scenes
+
+    scs = scenes.scene_batch()
+    nvox = sum(sc.grid.nvox for sc in scs)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    # sequential single-scene builds
+    pipes = []
+    for sc in scs:
+        v, t = torch.from_numpy(sc.verts).to(dev), torch.from_numpy(sc.tris).to(dev)
+        pipes.append((rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), device=dev), v, t, sc,
+                      rt.make_refine_params(sc.refine)))
+
+    def sequential():
+        for P, v, t, sc, rp in pipes:
+            P.rebuild(v, t, sc.jfa_steps, rp)
+
+    for _ in range(warmup):
+        sequential()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        sequential()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    seq_ms = ev[0].elapsed_time(ev[1]) / steps
+    seq_launches0 = rt.rtsdf_kernel_launches()
+    sequential()
+    torch.cuda.synchronize()
+    seq_launches = rt.rtsdf_kernel_launches() - seq_launches0
+    del pipes
+    torch.cuda.empty_cache()
+    # batched
+    B = rt.Batch(scs, device=dev)
+    tune_ms = B.autotune(reps=2)
+    for _ in range(warmup):
+        B.rebuild(0, False)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        B.rebuild(0, False)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    batch_ms = ev[0].elapsed_time(ev[1]) / steps
+    l0 = rt.rtsdf_kernel_launches()
+    B.rebuild(0, False)
+    torch.cuda.synchronize()
+    batch_launches = rt.rtsdf_kernel_launches() - l0
+    tri = sum(len(sc.tris) for sc in scs)
+    out = {"workload": f"{len(scs)} scenes, dims from {sorted(set(scenes.BATCH_DIMS))}, {tri} triangles, "
+                       f"{scs[0].refine.rays_per_voxel} rays/voxel, {nvox / 1e6:.1f} M voxels",
+           "batched_ms": round(batch_ms, 4), "sequential_ms": round(seq_ms, 4),
+           "batched_gvoxel_per_s": round(nvox / (batch_ms * 1e-3) / 1e9, 3),
+           "sequential_gvoxel_per_s": round(nvox / (seq_ms * 1e-3) / 1e9, 3),
+           "speedup": round(seq_ms / batch_ms, 3), "tuning": B.tuning, "autotune_refine_ms": round(tune_ms, 4),
+           "launches_batched": int(batch_launches), "launches_sequential": int(seq_launches), "steps": steps}
+    del B
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_backward(dev, steps: int = 10, warmup: int = 3) -> dict:
     """Forward + adjoint on the 128^3 differentiation workload (8 icospheres s3 +
     2 boxes, 65,536 field samples, 512x512 shadow image, 1 frame of 8 rays), against
@@ -429,9 +498,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h_verts.numel() * 4 + h_tris.numel() * 4),
                "d2h_bytes_per_step": int(h_sdf.numel() * 4 + h_vis.numel() * 4), "steps": ke}
 
-    bwd = None
+    bwd = batch = None
     if args.workload == "room" and not args.no_extensions:
         bwd = bench_backward(dev)
+        batch = bench_batch(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -446,7 +516,7 @@ def run_ours(args):
                 "rebuild_ms": round(rebuild_ms, 4),
                 "stage_ms": {k: round(v, 4) for k, v in stage.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "backward": bwd,
+                "backward": bwd, "batch": batch,
                 "clocks": clk, "counters": counters, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:

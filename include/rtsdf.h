@@ -270,6 +270,95 @@ rtsdf_status rtsdf_backward(const rtsdf_grid* g, const float* verts, int32_t V, 
                             const rtsdf_shadow_params* sp, const float* d_vis, float* d_verts, float* d_light,
                             void* ws, size_t ws_bytes, rtsdf_stream stream);
 
+/* ---------------------------------------------------------------- batched rebuild */
+
+/* No counterpart in the paper: many scenes of different grid sizes and meshes
+ * rebuilt together (voxelize, BVH, jump flooding, coarse field + ray mask,
+ * refinement; the steps of rtsdf_voxelize .. rtsdf_refine) with one launch per
+ * step for the whole batch instead of one per scene, the JFA pass chain replayed
+ * from a captured CUDA graph, and the refinement's brick shape and warps per CTA
+ * chosen by rtsdf_batch_autotune.  Every scene's outputs are bit-identical to its
+ * own single-scene calls with the same parameters. */
+
+#define RTSDF_BATCH_MAX_SCENES 64
+#define RTSDF_BATCH_MAX_STEPS 16
+
+typedef struct {
+    rtsdf_grid grid;
+    int32_t V, T;                         /* vertices and triangles of this scene's mesh */
+    int32_t nsteps;                       /* JFA offsets of this scene, 0..RTSDF_BATCH_MAX_STEPS */
+    int32_t steps[RTSDF_BATCH_MAX_STEPS]; /* each 1..1023, as rtsdf_jfa's steps */
+    rtsdf_refine_params refine;           /* frame_index and accumulate are set per rebuild call */
+} rtsdf_batch_scene;
+
+/* Where a scene lives in the batch's buffers (computed by the plan). */
+typedef struct {
+    int64_t voxel_offset;    /* first voxel in every batch grid array (a multiple of 64) */
+    int32_t vertex_offset;   /* first vertex in the batch vertex array */
+    int32_t triangle_offset; /* first triangle in the batch triangle array; its indices are local to the scene */
+    int64_t bvh_offset;      /* byte offset of the scene's BVH in the batch BVH buffer (256-aligned) */
+    int32_t flooded_in_b;    /* 1: the scene's flooded seeds end in buf_b, 0: in seed/buf_a */
+    int32_t reserved;
+} rtsdf_batch_layout;
+
+/* Refinement launch shape: bricks of brick_x * brick_y * brick_z = 64 voxels
+ * (brick_x in {4,8,16,32}, brick_y and brick_z in {1,2,4}), warps_per_cta in
+ * {1,2,4}; use_graph = 1 replays the JFA chain from a captured CUDA graph. */
+typedef struct {
+    int32_t brick_x, brick_y, brick_z;
+    int32_t warps_per_cta;
+    int32_t use_graph;
+} rtsdf_batch_tuning;
+
+/* Device buffers of a batch (all caller-owned; grid arrays hold rtsdf_batch_voxels
+ * elements, laid out per rtsdf_batch_layout). */
+typedef struct {
+    const float* verts;  /* [sum V][3] world, scene by scene */
+    const int32_t* tris; /* [sum T][3], indices local to each scene's vertices */
+    int32_t* seed;       /* in: nothing; out: voxelizer seeds, then JFA ping-pong buffer a */
+    int32_t* buf_b;      /* JFA ping-pong buffer b */
+    int32_t* rep_tri;    /* representative triangles (ids local to the scene) */
+    void* bvh;           /* rtsdf_batch_bvh_bytes bytes */
+    size_t bvh_bytes;
+    uint32_t* dist_bits; /* refinement state, as rtsdf_refine */
+    uint32_t* front;
+    uint32_t* back;
+    float* sdf;          /* signed field */
+    void* ws;            /* rtsdf_batch_workspace bytes */
+    size_t ws_bytes;
+} rtsdf_batch_buffers;
+
+typedef struct rtsdf_batch_plan rtsdf_batch_plan;
+
+/* Host-only: validates the scenes (1..RTSDF_BATCH_MAX_SCENES) and lays them out.
+ * The plan owns host memory, and after the first rebuild a CUDA stream and graph;
+ * destroy it with rtsdf_batch_plan_destroy.  It may be used from one host thread
+ * at a time. */
+rtsdf_status rtsdf_batch_plan_create(const rtsdf_batch_scene* scenes, int32_t S, rtsdf_batch_plan** plan);
+void rtsdf_batch_plan_destroy(rtsdf_batch_plan* plan);
+
+rtsdf_status rtsdf_batch_layout_of(const rtsdf_batch_plan* plan, int32_t scene, rtsdf_batch_layout* out);
+size_t rtsdf_batch_voxels(const rtsdf_batch_plan* plan);
+size_t rtsdf_batch_bvh_bytes(const rtsdf_batch_plan* plan);
+size_t rtsdf_batch_workspace(const rtsdf_batch_plan* plan);
+rtsdf_status rtsdf_batch_get_tuning(const rtsdf_batch_plan* plan, rtsdf_batch_tuning* out);
+rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_plan* plan, const rtsdf_batch_tuning* t);
+
+/* One frame of every scene: voxelize, BVH, JFA (each scene's own steps, aligned so
+ * that all scenes end on the last pass), coarse field and ray mask, refinement with
+ * ray ids frame_index*R + r and the given accumulate flag.  counters may be NULL
+ * (batch totals).  If the JFA graph is used, the first call with a given pair of
+ * JFA buffers captures it (on a stream of the plan) and later calls replay it. */
+rtsdf_status rtsdf_batch_rebuild(rtsdf_batch_plan* plan, const rtsdf_batch_buffers* b, uint32_t frame_index,
+                                 int32_t accumulate, rtsdf_counters* counters, rtsdf_stream stream);
+
+/* Times the refinement step of the batch under every supported tuning (reps
+ * launches each, after one rebuild with the current tuning), keeps the fastest in
+ * the plan and returns its time in *best_ms (host pointer, may be NULL).
+ * Synchronises the stream.  Leaves the buffers holding a frame-0 rebuild. */
+rtsdf_status rtsdf_batch_autotune(rtsdf_batch_plan* plan, const rtsdf_batch_buffers* b, int32_t reps,
+                                  float* best_ms, rtsdf_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 
 const char* rtsdf_status_string(rtsdf_status s);

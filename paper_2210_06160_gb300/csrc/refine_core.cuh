@@ -1,0 +1,465 @@
+// The per-tile and per-brick bodies of the coarse field / ray mask pass and of
+// the ray-sampled refinement (Sec. 2.1-2.3), shared by the single-scene kernels
+// (refine.cu) and the batched ones (batch.cu).  Templated on the brick shape
+// BX x BY x BZ (64 voxels, one bit each in a 64-bit mask): the resolve tile is
+// 32 x 4 x 4 voxels, so BX divides 32 and BY, BZ divide 4.
+#pragma once
+
+#include <float.h>
+
+#include "rtsdf_device.cuh"
+
+namespace rtsdf {
+
+constexpr int kListCap = 512;        // staged leaves per warp and round
+constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
+constexpr int kNarrowMargin = 96;    // > depth of any tree the builder makes (30-bit codes + 32 index bits)
+constexpr int kRaysPerLane = 8;      // rays of a voxel per group (one lane per voxel)
+constexpr int kFilterBatch = 4;      // staged triangles filtered per enqueue
+constexpr int kQueueCap = 32 + 32 * 8 * kFilterBatch;  // queued ray/triangle items per warp
+constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
+
+template <int BX, int BY, int BZ>
+struct BrickShape {
+    static_assert(BX * BY * BZ == 64, "a brick holds 64 voxels");
+    static_assert(32 % BX == 0 && 4 % BY == 0 && 4 % BZ == 0, "bricks tile the 32x4x4 resolve tile");
+    static constexpr int kPerTile = (32 / BX) * (4 / BY) * (4 / BZ);  // = 8
+};
+
+struct RefineArgs {
+    GridD g;
+    const float* verts;
+    int V;
+    const int32_t* tris;
+    int T;
+    float mask2;
+    float beta;
+    float empty_dist;
+    int R;
+    float tmax;
+    uint32_t k0, k1, frame, scene;
+    int accumulate, fallback;
+    int nbx, nby, nbz;  // brick grid
+};
+
+// One 32x4x4 tile of voxels (512 threads, tile coordinates tb): coarse distance u_c
+// to the representative triangle of the flooded seed; unmasked voxels get their
+// final value (u_c - beta); masked voxels initialise their refine state (and, when
+// tracked, the coarse source takes the winner record where it sets the distance).
+// The tile's bricks get 64-bit masks of their masked voxels from warp ballots, and
+// bricks with any masked voxel are appended to the work list as (tag | brick).
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ void resolve_tile(const RefineArgs& a, int3 tb, const int32_t* __restrict__ nearest,
+                                             const int32_t* __restrict__ rep_tri, uint32_t* __restrict__ dist_bits,
+                                             uint32_t* __restrict__ front, uint32_t* __restrict__ back,
+                                             float* __restrict__ sdf, unsigned long long* __restrict__ bmask,
+                                             int32_t* __restrict__ blist, uint32_t* __restrict__ count,
+                                             uint32_t* __restrict__ win_ray, int32_t* __restrict__ win_tri,
+                                             int32_t tag, unsigned long long* smask) {
+    constexpr int kBpx = 32 / BX, kBpy = 4 / BY;
+    const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz = threadIdx.x >> 7;
+    const int i = tb.x * 32 + tx, j = tb.y * 4 + ty, k = tb.z * 4 + tz;
+    if (threadIdx.x < 8) smask[threadIdx.x] = 0ull;
+    __syncthreads();
+    bool masked = false;
+    if (i < a.g.nx && j < a.g.ny && k < a.g.nz) {
+        const int64_t lin = ((int64_t)k * a.g.ny + j) * a.g.nx + i;
+        const int32_t s = __ldg(nearest + lin);
+        int32_t rep = -1;
+        int si = 0, sj = 0, sk = 0;
+        if (s != RTSDF_EMPTY) {
+            si = s & 1023;
+            sj = (s >> 10) & 1023;
+            sk = (s >> 20) & 1023;
+            rep = __ldg(rep_tri + ((int64_t)sk * a.g.ny + sj) * a.g.nx + si);
+        }
+        float uc = a.empty_dist;
+        float3 A, B, C;
+        if (rep >= 0 && load_tri(a.verts, a.V, a.tris, rep, a.g, A, B, C)) {
+            const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
+            uc = sqrtf(closest_d2(p, A, B, C));
+            const int dx = i - si, dy = j - sj, dz = k - sk;
+            masked = (float)(dx * dx + dy * dy + dz * dz) <= a.mask2;
+        }
+        // winner record (tracked calls): the coarse source holds a voxel's distance
+        // when the voxel is unmasked, starts fresh, or its coarse distance is lower
+        bool coarse_wins = true;
+        if (!masked) {
+            sdf[lin] = uc - a.beta;
+        } else {
+            const uint32_t ub = __float_as_uint(uc);
+            if (a.accumulate) {
+                const uint32_t old = dist_bits[lin];
+                coarse_wins = ub < old;
+                dist_bits[lin] = min(old, ub);
+            } else {
+                dist_bits[lin] = ub;
+                front[lin] = 0u;
+                back[lin] = 0u;
+            }
+        }
+        if (win_ray && coarse_wins) {
+            win_ray[lin] = 0xFFFFFFFFu;
+            win_tri[lin] = -1;
+        }
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, masked);
+    if (tx == 0 && bal) {
+        const int shift = ((tz % BZ) * BY + (ty % BY)) * BX;
+        const int row = ((tz / BZ) * kBpy + ty / BY) * kBpx;
+#pragma unroll
+        for (int b = 0; b < kBpx; ++b) {
+            const unsigned long long nib = (BX == 32) ? (unsigned long long)bal
+                                                      : (unsigned long long)((bal >> (BX * b)) & ((1u << BX) - 1u));
+            if (nib) atomicOr(&smask[row + b], nib << shift);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lb = threadIdx.x;
+        const int bx = tb.x * kBpx + lb % kBpx, by = tb.y * kBpy + (lb / kBpx) % kBpy,
+                  bz = tb.z * (4 / BZ) + lb / (kBpx * kBpy);
+        const bool valid = lb < 8 && bx < a.nbx && by < a.nby && bz < a.nbz;
+        const unsigned long long m = valid ? smask[lb] : 0ull;
+        const int64_t b = ((int64_t)bz * a.nby + by) * a.nbx + bx;
+        if (valid) bmask[b] = m;
+        const uint32_t act = __ballot_sync(0xffffffffu, m != 0ull);
+        uint32_t base = 0;
+        if (threadIdx.x == 0 && act) base = atomicAdd(count, (uint32_t)__popc(act));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (m) blist[base + __popc(act & ((1u << threadIdx.x) - 1u))] = tag | (int32_t)b;
+    }
+}
+
+// Does box [lo, hi] come within `ext` of the box [qlo, qhi] (the voxel centres of a
+// brick)?  Every point a ray of the brick can reach satisfies this, so boxes that
+// fail it hold no triangle any of the brick's rays can hit.
+__device__ __forceinline__ bool box_near(float4 lo, float4 hi, float3 qlo, float3 qhi, float ext2) {
+    const float gx = fmaxf(fmaxf(lo.x - qhi.x, qlo.x - hi.x), 0.0f);
+    const float gy = fmaxf(fmaxf(lo.y - qhi.y, qlo.y - hi.y), 0.0f);
+    const float gz = fmaxf(fmaxf(lo.z - qhi.z, qlo.z - hi.z), 0.0f);
+    return __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz)) <= ext2;
+}
+
+// Warp-cooperative walk of the BVH for the query region: pops up to 32 nodes per
+// step from the warp's stack and appends the leaves it reaches to `list`; stops
+// when the stack is empty or the list could overflow on the next step.  Returns
+// the new list length; `sp` is the stack depth.  A step grows the stack by at most
+// the nodes it pops, so once the stack is within kNarrowMargin of its capacity the
+// walk pops one node per step (depth first from the top): from there the stack
+// grows by at most the tree's depth, which stays below the margin.
+__device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes, int n_inner, int n_leaves,
+                                              float3 qlo, float3 qhi, float ext2, int* stack, int& sp,
+                                              int* list, int nc, bool& overflow) {
+    const int lane = threadIdx.x & 31;
+    int guard = 0;
+    while (sp > 0 && nc <= kListCap - 64) {
+        if (++guard > n_inner + 64) {  // a well-formed tree is exhausted long before
+            overflow = true;
+            sp = 0;
+            break;
+        }
+        const int take = sp > kStackCapW - kNarrowMargin ? 1 : min(sp, 32);
+        int node = -1;
+        if (lane < take) node = stack[sp - 1 - lane];
+        sp -= take;
+        bool h0 = false, h1 = false;
+        int c0 = 0, c1 = 0;
+        if (node >= 0 && node < n_inner) {
+            const BvhNode* nd = nodes + node;
+            const float4 lo0 = __ldg(&nd->lo0), hi0 = __ldg(&nd->hi0);
+            const float4 lo1 = __ldg(&nd->lo1), hi1 = __ldg(&nd->hi1);
+            c0 = __float_as_int(lo0.w);
+            c1 = __float_as_int(hi0.w);
+            h0 = box_near(lo0, hi0, qlo, qhi, ext2);
+            h1 = n_leaves > 1 && box_near(lo1, hi1, qlo, qhi, ext2);
+            if (c0 < 0 && ~c0 >= n_leaves) h0 = false;
+            if (c1 < 0 && ~c1 >= n_leaves) h1 = false;
+        }
+        const int np = (h0 && c0 >= 0) + (h1 && c1 >= 0);
+        const int nl = (h0 && c0 < 0) + (h1 && c1 < 0);
+        int pp = np, pl = nl;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, pp, off);
+            const int v = __shfl_up_sync(0xffffffffu, pl, off);
+            if (lane >= off) {
+                pp += u;
+                pl += v;
+            }
+        }
+        const int tot_p = __shfl_sync(0xffffffffu, pp, 31);
+        const int tot_l = __shfl_sync(0xffffffffu, pl, 31);
+        int wp = sp + pp - np;
+        if (h0 && c0 >= 0) { if (wp < kStackCapW) stack[wp] = c0; ++wp; }
+        if (h1 && c1 >= 0) { if (wp < kStackCapW) stack[wp] = c1; ++wp; }
+        int wl = nc + pl - nl;
+        if (h0 && c0 < 0) list[wl++] = ~c0;
+        if (h1 && c1 < 0) list[wl++] = ~c1;
+        if (sp + tot_p > kStackCapW) {
+            overflow = true;
+            sp = kStackCapW;
+        } else {
+            sp += tot_p;
+        }
+        nc += tot_l;
+        __syncwarp();
+    }
+    return nc;
+}
+
+// Per-warp shared state of k_refine.
+struct WarpSmem {
+    int list[kListCap];             // staged leaves
+    int stack[kStackCapW];
+    uint32_t queue[kQueueCap];      // (list index << 8) | (slot << 3) | ray
+    int qn;                         // queued items
+    float4 origin[32];              // voxel centres of the pass's slots
+    float4 dir[8][32];              // ray directions of the group, [ray][slot]
+    unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
+};
+
+// Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
+// closest hit per ray (ties to the lower id) is kept with a 64-bit atomicMin.
+__device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
+                                         float tmax) {
+    const int c = (int)(item >> 8), slot = (int)((item >> 3) & 31u), r = (int)(item & 7u);
+    const float4 of = w.origin[slot], df = w.dir[r][slot];
+    const float3 o = make_float3(of.x, of.y, of.z), d = make_float3(df.x, df.y, df.z);
+    const BvhLeaf* L = leaves + w.list[c];
+    const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
+    const float3 A = make_float3(v0.x, v0.y, v0.z);
+    const float3 e1 = make_float3(e1f.x, e1f.y, e1f.z), e2 = make_float3(e2f.x, e2f.y, e2f.z);
+    float t;
+    bool front;
+    if (ray_tri(o, d, A, e1, e2, tmax, t, front)) {
+        const uint32_t id = (uint32_t)__float_as_int(v0.w);
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)((id << 1) | (front ? 1u : 0u));
+        atomicMin(&w.key[r][slot], key);
+    }
+}
+
+// Which of this lane's rays can hit the triangle of `leaf`: the (voxel, triangle)
+// pair must be within reach of the bounding sphere; each ray's line must pass
+// within rho of the sphere centre with the centre at most rho behind the origin
+// (off the rho-sphere by more than rho*sqrt(2) that is exactly tc >= sqrt(dd -
+// rho^2); nearer, tc >= -rho is kept, a superset); and the ray must head for the
+// triangle's plane and cross it within the ray length.  All margins exceed the
+// FP32 rounding of both sides, so no triangle the exact test accepts is dropped.
+__device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf, float3 o, uint32_t okm,
+                                                const float2* dx2, const float2* dy2, const float2* dz2,
+                                                float tmax) {
+    const float4 sph = __ldg(&leaf->sph);
+    const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
+    const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
+    const float reach = sph.w + tmax;
+    if (!okm || dd > reach * reach) return 0u;
+    const float4 pl = __ldg(&leaf->pln);
+    const float rho = sph.w;
+    const float rho2 = rho * rho;
+    const float thr = dd > 2.0f * rho2 ? __fsqrt_rn(dd - rho2) * 0.999999f - 1e-4f : -rho;
+    const float sd = pl.w - __fmaf_rn(pl.x, o.x, __fmaf_rn(pl.y, o.y, pl.z * o.z));
+    const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
+    const float asd = fabsf(sd);
+    const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
+    const float2 nx2 = make_float2(pl.x, pl.x), ny2 = make_float2(pl.y, pl.y), nz2 = make_float2(pl.z, pl.z);
+    uint32_t pm = 0;
+#pragma unroll
+    for (int r = 0; r < kRaysPerLane / 2; ++r) {
+        const float2 tc = __ffma2_rn(cx2, dx2[r], __ffma2_rn(cy2, dy2[r], __fmul2_rn(cz2, dz2[r])));
+        const float2 dn = __ffma2_rn(nx2, dx2[r], __ffma2_rn(ny2, dy2[r], __fmul2_rn(nz2, dz2[r])));
+        const bool ok0 = tc.x >= thr && sd * dn.x > -eps && asd <= __fmaf_rn(tmax, fabsf(dn.x), eps);
+        const bool ok1 = tc.y >= thr && sd * dn.y > -eps && asd <= __fmaf_rn(tmax, fabsf(dn.y), eps);
+        pm |= ((ok0 ? 1u : 0u) << (2 * r)) | ((ok1 ? 1u : 0u) << (2 * r + 1));
+    }
+    return pm & okm;
+}
+
+
+// One warp refines one brick (bx, by, bz) whose masked voxels are the set bits of
+// m; lane l owns voxel slot (pass*32 + l) and up to 8 rays of it per group.  For
+// every staged triangle the lane culls the (voxel, triangle) pair by the
+// triangle's bounding sphere grown by the ray length, then each ray by the
+// distance of the sphere's centre to the ray's line (and the side it lies on).
+// Surviving (voxel, ray, triangle) items are queued in shared memory and run
+// through the exact ray/triangle test 32 at a time, so the expensive test does
+// not diverge.  Both filters are conservative (their margins exceed FP32 rounding
+// of the exact test), so they never drop a triangle the exact test accepts; they
+// may use fused multiply-adds because they decide nothing the oracle decides.
+template <int BX, int BY, int BZ, bool kTrack>
+__device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode* __restrict__ nodes,
+                                             const BvhLeaf* __restrict__ leaves, int n_leaves, int n_inner,
+                                             const int32_t* __restrict__ nearest,
+                                             const int32_t* __restrict__ rep_tri, unsigned long long m, int bx,
+                                             int by, int bz, uint32_t* __restrict__ dist_bits,
+                                             uint32_t* __restrict__ front, uint32_t* __restrict__ back,
+                                             float* __restrict__ sdf, uint32_t* __restrict__ win_ray,
+                                             int32_t* __restrict__ win_tri, WarpSmem& w, uint32_t& n_hit,
+                                             uint32_t& n_fail, uint32_t& n_ovf) {
+    const int lane = threadIdx.x & 31;
+    const float ext = a.tmax * 1.00001f + 1e-3f;
+    const int nm = __popcll(m);
+    // every ray of the brick stays inside its voxel centres' box grown by the ray length
+    const float3 qlo = make_float3((float)(bx * BX) + 0.5f, (float)(by * BY) + 0.5f, (float)(bz * BZ) + 0.5f);
+    const float3 qhi = make_float3((float)(bx * BX + BX - 1) + 0.5f, (float)(by * BY + BY - 1) + 0.5f,
+                                   (float)(bz * BZ + BZ - 1) + 0.5f);
+    bool overflow = false;
+    // walk once for the whole brick; the list is reused by every pass and ray
+    // group unless it overflowed, in which case each pass walks again in rounds
+    int sp0 = 0;
+    if (n_leaves > 0) {
+        if (lane == 0) w.stack[0] = 0;
+        sp0 = 1;
+    }
+    __syncwarp();
+    const int nc_all = walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack, sp0, w.list, 0,
+                                      overflow);
+    const bool complete = sp0 == 0;
+    for (int pass = 0; pass * 32 < nm; ++pass) {
+        const int slot = pass * 32 + lane;
+        const bool mine = slot < nm;
+        int lin = 0;
+        float3 o = make_float3(0.f, 0.f, 0.f);
+        if (mine) {
+            // position of the slot-th set bit of the brick mask
+            unsigned long long mm = m;
+            int skip = slot;
+            const int lo_cnt = __popc((uint32_t)mm);
+            if (skip >= lo_cnt) {
+                skip -= lo_cnt;
+                mm &= 0xffffffff00000000ull;
+            }
+            for (int c = 0; c < skip; ++c) mm &= mm - 1ull;
+            const int bit = __ffsll((long long)mm) - 1;
+            const int i = bx * BX + bit % BX, j = by * BY + (bit / BX) % BY, k = bz * BZ + bit / (BX * BY);
+            lin = (int)(((int64_t)k * a.g.ny + j) * a.g.nx + i);
+            o = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
+        }
+        w.origin[lane] = make_float4(o.x, o.y, o.z, 0.f);
+        uint32_t vbest = 0xffffffffu, vfront = 0, vback = 0;
+        // tracked: this call's winning ray, ordered by (t, triangle id), first ray on ties
+        unsigned long long wkey = ~0ull;
+        uint32_t wray = 0xFFFFFFFFu;
+        for (int r0 = 0; r0 < a.R; r0 += kRaysPerLane) {
+            float3 dir[kRaysPerLane];
+            uint32_t okm = 0;
+#pragma unroll
+            for (int r = 0; r < kRaysPerLane; ++r) {
+                const int ray = r0 + r;
+                dir[r] = make_float3(0.f, 0.f, 1.f);
+                if (mine && ray < a.R) {
+                    if (sphere_dir((uint32_t)lin, a.frame * (uint32_t)a.R + (uint32_t)ray, a.scene, a.k0, a.k1,
+                                   dir[r]))
+                        okm |= 1u << r;
+                    else
+                        ++n_fail;
+                }
+                w.dir[r][lane] = make_float4(dir[r].x, dir[r].y, dir[r].z, 0.f);
+                w.key[r][lane] = ~0ull;
+            }
+            float2 dx2[kRaysPerLane / 2], dy2[kRaysPerLane / 2], dz2[kRaysPerLane / 2];
+#pragma unroll
+            for (int r = 0; r < kRaysPerLane / 2; ++r) {
+                dx2[r] = make_float2(dir[2 * r].x, dir[2 * r + 1].x);
+                dy2[r] = make_float2(dir[2 * r].y, dir[2 * r + 1].y);
+                dz2[r] = make_float2(dir[2 * r].z, dir[2 * r + 1].z);
+            }
+            int sp = 0;
+            if (!complete && n_leaves > 0) {
+                if (lane == 0) w.stack[0] = 0;
+                sp = 1;
+            }
+            __syncwarp();
+            bool first = true;
+            while (first || sp > 0) {
+                first = false;
+                const int nc = complete ? nc_all
+                                        : walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack,
+                                                         sp, w.list, 0, overflow);
+                if (lane == 0) w.qn = 0;
+                __syncwarp();
+                for (int c0 = 0; c0 < nc; c0 += kFilterBatch) {
+                    // filter kFilterBatch staged triangles (independent work), then each lane
+                    // that has survivors claims queue slots with one shared atomic
+                    uint32_t pm4 = 0;  // bit (j * 8 + r): ray r vs triangle c0 + j
+#pragma unroll
+                    for (int j = 0; j < kFilterBatch; ++j) {
+                        const int c = c0 + j;
+                        if (c < nc) pm4 |= filter_rays(leaves + w.list[c], o, okm, dx2, dy2, dz2, a.tmax) << (8 * j);
+                    }
+                    if (pm4) {
+                        int pos = atomicAdd(&w.qn, __popc(pm4));
+                        while (pm4) {
+                            const int bit = __ffs(pm4) - 1;
+                            pm4 &= pm4 - 1u;
+                            w.queue[pos++] =
+                                ((uint32_t)(c0 + (bit >> 3)) << 8) | ((uint32_t)lane << 3) | (uint32_t)(bit & 7);
+                        }
+                    }
+                    __syncwarp();
+                    int qn = w.qn;
+                    if (qn >= 32) {
+                        while (qn >= 32) {
+                            run_item(w, leaves, w.queue[qn - 32 + lane], a.tmax);
+                            qn -= 32;
+                        }
+                        __syncwarp();
+                        if (lane == 0) w.qn = qn;
+                        __syncwarp();
+                    }
+                }
+                {
+                    const int qn = w.qn;
+                    if (lane < qn) run_item(w, leaves, w.queue[lane], a.tmax);
+                    __syncwarp();
+                }
+                __syncwarp();
+                __syncwarp();
+            }
+            // closest hits of this lane's rays
+#pragma unroll
+            for (int r = 0; r < kRaysPerLane; ++r) {
+                const unsigned long long key = w.key[r][lane];
+                if (key != ~0ull) {
+                    vbest = min(vbest, (uint32_t)(key >> 32));
+                    if (key & 1ull) ++vfront; else ++vback;
+                    ++n_hit;
+                    if (kTrack && (key >> 1) < wkey) {
+                        wkey = key >> 1;
+                        wray = a.frame * (uint32_t)a.R + (uint32_t)(r0 + r);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (mine) {
+            const uint32_t old = dist_bits[lin];
+            const uint32_t d = min(old, vbest);
+            if (kTrack && vbest < old) {
+                win_ray[lin] = wray;
+                win_tri[lin] = (int32_t)(wkey & 0x7FFFFFFFull);
+            }
+            const uint32_t fr = front[lin] + vfront, bk = back[lin] + vback;
+            dist_bits[lin] = d;
+            front[lin] = fr;
+            back[lin] = bk;
+            bool neg = bk > fr;
+            if (fr == bk && a.fallback) {
+                const int32_t s = nearest[lin];
+                const int64_t sl2 =
+                    ((int64_t)((s >> 20) & 1023) * a.g.ny + ((s >> 10) & 1023)) * a.g.nx + (s & 1023);
+                float3 A, B, C;
+                load_tri(a.verts, a.V, a.tris, rep_tri[sl2], a.g, A, B, C);
+                const float3 n = cross3(sub3(B, A), sub3(C, A));
+                neg = dot3(sub3(o, A), n) < 0.0f;
+            }
+            const float df = __uint_as_float(d);
+            sdf[lin] = neg ? -df : df;
+        }
+        __syncwarp();
+    }
+    n_ovf += overflow ? 1u : 0u;
+}
+
+}  // namespace rtsdf

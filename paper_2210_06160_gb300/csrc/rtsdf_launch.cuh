@@ -45,6 +45,15 @@ size_t voxelize_workspace(int32_t T, const rtsdf_grid& g);
 rtsdf_status voxelize(const float* verts, int32_t V, const int32_t* tris, int32_t T, const rtsdf_grid& g,
                       int32_t* seed, int32_t* rep_tri, void* ws, rtsdf_counters* counters, cudaStream_t s);
 
+// Stable LSD radix sort of (key, value) pairs over the low key_bits bits, 8 bits
+// per pass, ping-ponging between (ka, va) and (kb, vb); *sorted_* name the buffers
+// holding the result.  K is uint32_t or unsigned long long.
+template <typename K>
+size_t radix_sort_scratch(int n);
+template <typename K>
+rtsdf_status radix_sort_pairs(K* ka, uint32_t* va, K* kb, uint32_t* vb, int n, int key_bits, void* scratch,
+                              cudaStream_t s, K** sorted_k, uint32_t** sorted_v);
+
 size_t bvh_bytes(int32_t T);
 size_t bvh_workspace(int32_t T);
 rtsdf_status build_bvh(const float* verts, int32_t V, const int32_t* tris, int32_t T, const rtsdf_grid& g,

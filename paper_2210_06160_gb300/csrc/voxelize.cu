@@ -9,34 +9,12 @@
 // the voxel test on the voxels of (brick ∩ triangle range); an overlapping voxel
 // takes the 64-bit key (float bits of the closest-point distance^2, triangle id)
 // with atomicMin, which is the argmin with ties to the lower id in any order.
-#include "rtsdf_device.cuh"
 #include "rtsdf_launch.cuh"
+#include "voxelize_core.cuh"
 
 namespace rtsdf {
 
-constexpr int kBrick = 8;
 constexpr int kChunk = 16;  // items per warp chunk
-
-// Voxel range of a triangle along one axis: the closed triangle can touch voxel i
-// (spanning [i, i+1]) only if min <= i + 1 and max >= i.
-__device__ __forceinline__ bool axis_range(float a, float b, float c, int n, int& lo, int& hi) {
-    const float mn = fminf(fminf(a, b), c), mx = fmaxf(fmaxf(a, b), c);
-    const float l = fmaxf(ceilf(mn) - 1.0f, 0.0f);
-    const float h = fminf(floorf(mx), (float)n - 1.0f);
-    if (!(l <= h)) return false;
-    lo = (int)l;
-    hi = (int)h;
-    return true;
-}
-
-struct TriRange {
-    int lo[3], hi[3];
-};
-
-__device__ __forceinline__ bool tri_range(float3 a, float3 b, float3 c, const GridD& g, TriRange& r) {
-    return axis_range(a.x, b.x, c.x, g.nx, r.lo[0], r.hi[0]) && axis_range(a.y, b.y, c.y, g.ny, r.lo[1], r.hi[1]) &&
-           axis_range(a.z, b.z, c.z, g.nz, r.lo[2], r.hi[2]);
-}
 
 // Per triangle: number of bricks its voxel range touches (0 if invalid or outside).
 __global__ void k_vox_count(const float* __restrict__ verts, int V, const int32_t* __restrict__ tris, int T,
@@ -49,10 +27,7 @@ __global__ void k_vox_count(const float* __restrict__ verts, int V, const int32_
         if (counters) atomicAdd(&counters->skipped_triangles, 1u);
     } else {
         TriRange r;
-        if (tri_range(a, b, c, g, r)) {
-            n = (uint32_t)((r.hi[0] / kBrick - r.lo[0] / kBrick + 1) * (r.hi[1] / kBrick - r.lo[1] / kBrick + 1) *
-                           (r.hi[2] / kBrick - r.lo[2] / kBrick + 1));
-        }
+        if (tri_range(a, b, c, g, r)) n = range_bricks(r);
     }
     counts[t] = n;
 }
@@ -61,7 +36,6 @@ __global__ void __launch_bounds__(256) k_vox_test(const float* __restrict__ vert
                                                   const int32_t* __restrict__ tris, int T, GridD g,
                                                   const uint64_t* __restrict__ offsets,  // T+1 exclusive scan
                                                   unsigned long long* __restrict__ keys) {
-    const uint32_t lane = lane_id();
     const int64_t warp = (int64_t)(blockIdx.x * blockDim.x + threadIdx.x) / kWarp;
     const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / kWarp;
     const uint64_t total = offsets[T];
@@ -77,39 +51,15 @@ __global__ void __launch_bounds__(256) k_vox_test(const float* __restrict__ vert
         int t = lo;
         float3 a, b, c;
         TriRange r;
-        int nbx = 0, nby = 0;
         bool have = false;
         for (uint64_t item = i0; item < i1; ++item) {
             while (offsets[t + 1] <= item) { ++t; have = false; }
             if (!have) {
                 load_tri(verts, V, tris, t, g, a, b, c);  // count > 0 implies valid
                 tri_range(a, b, c, g, r);
-                nbx = r.hi[0] / kBrick - r.lo[0] / kBrick + 1;
-                nby = r.hi[1] / kBrick - r.lo[1] / kBrick + 1;
                 have = true;
             }
-            const int local = (int)(item - offsets[t]);
-            const int bx = r.lo[0] / kBrick + local % nbx;
-            const int by = r.lo[1] / kBrick + (local / nbx) % nby;
-            const int bz = r.lo[2] / kBrick + local / (nbx * nby);
-            // brick cull with a margin far above FP32 rounding of the voxel test
-            const float3 bc = make_float3((float)(bx * kBrick) + 0.5f * kBrick, (float)(by * kBrick) + 0.5f * kBrick,
-                                          (float)(bz * kBrick) + 0.5f * kBrick);
-            if (!tri_box_overlap(a, b, c, bc, 0.5f * kBrick + 0.0625f)) continue;
-            const int x0 = max(r.lo[0], bx * kBrick), x1 = min(r.hi[0], bx * kBrick + kBrick - 1);
-            const int y0 = max(r.lo[1], by * kBrick), y1 = min(r.hi[1], by * kBrick + kBrick - 1);
-            const int z0 = max(r.lo[2], bz * kBrick), z1 = min(r.hi[2], bz * kBrick + kBrick - 1);
-            const int sx = x1 - x0 + 1, sy = y1 - y0 + 1, nsub = sx * sy * (z1 - z0 + 1);
-            for (int v = (int)lane; v < nsub; v += kWarp) {
-                const int i = x0 + v % sx, j = y0 + (v / sx) % sy, k = z0 + v / (sx * sy);
-                const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
-                if (!tri_box_overlap(a, b, c, p, 0.5f)) continue;
-                const float d2 = closest_d2(p, a, b, c);
-                const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned long long)(uint32_t)t;
-                const int64_t lin = ((int64_t)k * g.ny + j) * g.nx + i;
-                atomicMin(keys + lin, key);
-            }
+            vox_item(a, b, c, r, (int)(item - offsets[t]), t, g, keys);
         }
     }
 }

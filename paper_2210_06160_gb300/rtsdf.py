@@ -53,6 +53,31 @@ class Counters(C.Structure):
 
 COUNTER_FIELDS = [f for f, _ in Counters._fields_ if f != "reserved"]
 
+BATCH_MAX_SCENES = 64
+BATCH_MAX_STEPS = 16
+
+
+class BatchScene(C.Structure):
+    _fields_ = [("grid", Grid), ("V", C.c_int32), ("T", C.c_int32), ("nsteps", C.c_int32),
+                ("steps", C.c_int32 * BATCH_MAX_STEPS), ("refine", RefineParams)]
+
+
+class BatchLayout(C.Structure):
+    _fields_ = [("voxel_offset", C.c_int64), ("vertex_offset", C.c_int32), ("triangle_offset", C.c_int32),
+                ("bvh_offset", C.c_int64), ("flooded_in_b", C.c_int32), ("reserved", C.c_int32)]
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("brick_x", C.c_int32), ("brick_y", C.c_int32), ("brick_z", C.c_int32),
+                ("warps_per_cta", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class BatchBuffers(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("tris", C.c_void_p), ("seed", C.c_void_p), ("buf_b", C.c_void_p),
+                ("rep_tri", C.c_void_p), ("bvh", C.c_void_p), ("bvh_bytes", C.c_size_t),
+                ("dist_bits", C.c_void_p), ("front", C.c_void_p), ("back", C.c_void_p), ("sdf", C.c_void_p),
+                ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+
 _P = C.c_void_p
 _SIGS = {
     "rtsdf_version": (C.c_int32, []),
@@ -77,6 +102,16 @@ _SIGS = {
     "rtsdf_backward": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P,
                                  C.POINTER(RefineParams), _P, _P, C.c_int32, _P, _P, _P, C.c_int32,
                                  C.POINTER(ShadowParams), _P, _P, _P, _P, C.c_size_t, _P]),
+    "rtsdf_batch_plan_create": (C.c_int, [C.POINTER(BatchScene), C.c_int32, C.POINTER(C.c_void_p)]),
+    "rtsdf_batch_plan_destroy": (None, [_P]),
+    "rtsdf_batch_layout_of": (C.c_int, [_P, C.c_int32, C.POINTER(BatchLayout)]),
+    "rtsdf_batch_voxels": (C.c_size_t, [_P]),
+    "rtsdf_batch_bvh_bytes": (C.c_size_t, [_P]),
+    "rtsdf_batch_workspace": (C.c_size_t, [_P]),
+    "rtsdf_batch_get_tuning": (C.c_int, [_P, C.POINTER(BatchTuning)]),
+    "rtsdf_batch_set_tuning": (C.c_int, [_P, C.POINTER(BatchTuning)]),
+    "rtsdf_batch_rebuild": (C.c_int, [_P, C.POINTER(BatchBuffers), C.c_uint32, C.c_int32, _P, _P]),
+    "rtsdf_batch_autotune": (C.c_int, [_P, C.POINTER(BatchBuffers), C.c_int32, C.POINTER(C.c_float), _P]),
 }
 
 BACKWARD_MAX_STEPS = 512
@@ -399,3 +434,114 @@ class SDFShadow(torch.autograd.Function):
 def sdf_shadow(verts, light, pipe, tris, jfa_steps, frames, pts, pos, nrm, shadow):
     """Differentiable field samples and shadow image (see SDFShadow)."""
     return SDFShadow.apply(verts, light, pipe, tris, jfa_steps, frames, pts, pos, nrm, shadow)
+
+
+# ------------------------------------------------------------ batched rebuild
+
+def make_batch_scene(grid, n_verts: int, n_tris: int, steps, refine) -> BatchScene:
+    steps = [int(k) for k in steps]
+    if len(steps) > BATCH_MAX_STEPS:
+        raise RtsdfError(f"at most {BATCH_MAX_STEPS} JFA steps per scene")
+    arr = (C.c_int32 * BATCH_MAX_STEPS)(*(steps + [0] * (BATCH_MAX_STEPS - len(steps))))
+    return BatchScene(make_grid(grid), int(n_verts), int(n_tris), len(steps), arr, make_refine_params(refine))
+
+
+def rtsdf_batch_plan_create(scenes: list) -> C.c_void_p:
+    arr = (BatchScene * len(scenes))(*scenes)
+    plan = C.c_void_p()
+    _check(lib().rtsdf_batch_plan_create(arr, len(scenes), C.byref(plan)), "rtsdf_batch_plan_create")
+    return plan
+
+
+def rtsdf_batch_rebuild(plan, buffers: BatchBuffers, frame_index: int, accumulate: bool, counters=None,
+                        stream=None) -> None:
+    _check(lib().rtsdf_batch_rebuild(plan, C.byref(buffers), int(frame_index) & 0xFFFFFFFF, int(bool(accumulate)),
+                                     _dev(counters, torch.int32, "counters"), _stream(stream)), "rtsdf_batch_rebuild")
+
+
+def rtsdf_batch_autotune(plan, buffers: BatchBuffers, reps: int = 3, stream=None) -> float:
+    ms = C.c_float()
+    _check(lib().rtsdf_batch_autotune(plan, C.byref(buffers), int(reps), C.byref(ms), _stream(stream)),
+           "rtsdf_batch_autotune")
+    return float(ms.value)
+
+
+class Batch:
+    """Device buffers and plan of a batch of scenes (rtsdf_batch_*): meshes are
+    concatenated scene by scene, grids laid out at the plan's voxel offsets.
+
+    `scenes`: objects with grid, verts [V,3], tris [T,3] (indices local to the
+    scene), jfa_steps and refine (e.g. scenes.Scene); scene ids come from each
+    scene's refine parameters.
+    """
+
+    def __init__(self, scenes: list, device="cuda"):
+        if not 1 <= len(scenes) <= BATCH_MAX_SCENES:
+            raise RtsdfError(f"a batch holds 1..{BATCH_MAX_SCENES} scenes")
+        self.scenes = scenes
+        self.desc = [make_batch_scene(sc.grid, len(sc.verts), len(sc.tris), sc.jfa_steps, sc.refine) for sc in scenes]
+        self.plan = rtsdf_batch_plan_create(self.desc)
+        L = lib()
+        self.layout = []
+        for i in range(len(scenes)):
+            lay = BatchLayout()
+            _check(L.rtsdf_batch_layout_of(self.plan, i, C.byref(lay)), "rtsdf_batch_layout_of")
+            self.layout.append(lay)
+        dev = torch.device(device)
+        self.nvox = int(L.rtsdf_batch_voxels(self.plan))
+        import numpy as np
+        self.verts = torch.from_numpy(np.concatenate([np.asarray(sc.verts, np.float32) for sc in scenes])
+                                      .reshape(-1, 3)).to(dev)
+        self.tris = torch.from_numpy(np.concatenate([np.asarray(sc.tris, np.int32) for sc in scenes])
+                                     .reshape(-1, 3)).to(dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.seed = torch.empty(self.nvox, **i32)
+        self.buf_b = torch.empty(self.nvox, **i32)
+        self.rep_tri = torch.empty(self.nvox, **i32)
+        self.dist_bits = torch.full((self.nvox,), 0x7F800000, **i32)
+        self.front = torch.zeros(self.nvox, **i32)
+        self.back = torch.zeros(self.nvox, **i32)
+        self.sdf = torch.empty(self.nvox, dtype=torch.float32, device=dev)
+        self.bvh = torch.empty(max(256, int(L.rtsdf_batch_bvh_bytes(self.plan))), dtype=torch.uint8, device=dev)
+        self.ws = torch.empty(int(L.rtsdf_batch_workspace(self.plan)), dtype=torch.uint8, device=dev)
+        self.counters = torch.zeros(8, **i32)
+        self.buffers = BatchBuffers(self.verts.data_ptr(), self.tris.data_ptr(), self.seed.data_ptr(),
+                                    self.buf_b.data_ptr(), self.rep_tri.data_ptr(), self.bvh.data_ptr(),
+                                    self.bvh.numel(), self.dist_bits.data_ptr(), self.front.data_ptr(),
+                                    self.back.data_ptr(), self.sdf.data_ptr(), self.ws.data_ptr(), self.ws.numel())
+
+    def rebuild(self, frame_index: int = 0, accumulate: bool = False, stream=None):
+        rtsdf_batch_rebuild(self.plan, self.buffers, frame_index, accumulate, self.counters, stream)
+
+    def autotune(self, reps: int = 3, stream=None) -> float:
+        return rtsdf_batch_autotune(self.plan, self.buffers, reps, stream)
+
+    @property
+    def tuning(self) -> dict:
+        t = BatchTuning()
+        _check(lib().rtsdf_batch_get_tuning(self.plan, C.byref(t)), "rtsdf_batch_get_tuning")
+        return {f: int(getattr(t, f)) for f, _ in BatchTuning._fields_}
+
+    def set_tuning(self, brick=(4, 4, 4), warps_per_cta=2, use_graph=True):
+        t = BatchTuning(int(brick[0]), int(brick[1]), int(brick[2]), int(warps_per_cta), int(bool(use_graph)))
+        _check(lib().rtsdf_batch_set_tuning(self.plan, C.byref(t)), "rtsdf_batch_set_tuning")
+
+    def view(self, i: int, name: str) -> torch.Tensor:
+        """Scene i's slice of a batch grid array, shaped (nz, ny, nx); 'nearest' is
+        the buffer holding its flooded seeds."""
+        sc, lay = self.scenes[i], self.layout[i]
+        g = sc.grid
+        if name == "nearest":
+            name = "buf_b" if lay.flooded_in_b else "seed"
+        a = getattr(self, name)
+        o = int(lay.voxel_offset)
+        return a[o:o + g.nx * g.ny * g.nz].view(g.nz, g.ny, g.nx)
+
+    def __del__(self):
+        plan = getattr(self, "plan", None)
+        if plan is not None and plan.value:
+            try:
+                lib().rtsdf_batch_plan_destroy(plan)
+            except Exception:
+                pass
+            self.plan = None

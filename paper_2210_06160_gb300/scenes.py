@@ -360,3 +360,68 @@ def scene_diff(n: int = 128, subdiv: int = 3, n_spheres: int = 8, n_boxes: int =
     pts = rng.uniform(0.0, 1.0, size=(n_samples, 3)).astype(np.float32)
     vt = (V + rng.normal(0.0, noise, size=V.shape)).astype(np.float32)
     return DiffScene(sc, pts, vt)
+
+
+BATCH_DIMS = ((32, 32, 32), (64, 64, 64), (128, 128, 128), (96, 48, 96), (200, 100, 200), (256, 128, 256))
+
+
+def scene_batch(n: int = 48, seed: int = 4848, dims_choices=BATCH_DIMS, tri_range=(500, 60_000),
+                rays: int = 8, shadow_res: int = 16) -> list[Scene]:
+    """Seeded scenes of uneven sizes for the batched rebuild: grid dims drawn from
+    `dims_choices` (h = 2 / largest dim, so each box is at most 2 wide), a ground
+    quad plus primitives of the room mix (icospheres, boxes, tori) with random
+    pose and scale 0.05-0.3 added until the scene holds a triangle count drawn
+    uniformly from `tri_range`; scene i has scene id i."""
+    rng = np.random.default_rng(seed)
+    kinds = [("sphere2", lambda: icosphere(2)), ("sphere3", lambda: icosphere(3)), ("sphere4", lambda: icosphere(4)),
+             ("box", box_mesh), ("torus32", lambda: torus_mesh(32, 16, 0.3)), ("torus64", lambda: torus_mesh(64, 32, 0.3))]
+    cache = {}
+    out = []
+    for i in range(n):
+        nx, ny, nz = dims_choices[int(rng.integers(len(dims_choices)))]
+        h = 2.0 / max(nx, ny, nz)
+        box = (nx * h, ny * h, nz * h)
+        target = int(rng.integers(tri_range[0], tri_range[1] + 1))
+        parts = [quad_mesh(0.05 * box[1], 0.0, box[0], 0.0, box[2])]
+        total = 2
+        while total < target:
+            name, make = kinds[int(rng.integers(len(kinds)))]
+            if name not in cache:
+                cache[name] = make()
+            Vp, Tp = cache[name]
+            c = np.array([rng.uniform(0.1, b - 0.1) for b in box])
+            s = rng.uniform(0.05, 0.3)
+            parts.append(((Vp * s) @ random_rotation(rng).T + c, Tp))
+            total += len(Tp)
+        V, T = merge(parts)
+        g = Grid(nx, ny, nz, (0.0, 0.0, 0.0), h)
+        pos, nrm = receivers_plane(0.05 * box[1], 0.0, box[0], 0.0, box[2], shadow_res, shadow_res)
+        out.append(Scene(f"batch{i}-{nx}x{ny}x{nz}", V.astype(np.float32), T, g,
+                         RefineParams(mask_vox=4.0, rays_per_voxel=rays, max_ray_vox=8.0, beta_vox=1.0,
+                                      key=(0xB47C, 0x4848), scene_id=i),
+                         ShadowParams(steps=64, max_step_vox=0.05 / h), jfa_steps(g), 1, pos, nrm))
+    return out
+
+
+def scene_batch_small(seed: int = 77) -> list[Scene]:
+    """A few small scenes of ragged sizes whose oracle rebuilds finish in seconds."""
+    dims = ((32, 32, 32), (24, 16, 20), (40, 24, 32), (17, 33, 9), (8, 8, 8), (33, 20, 27))
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, (nx, ny, nz) in enumerate(dims):
+        h = 1.0 / max(nx, ny, nz)
+        box = (nx * h, ny * h, nz * h)
+        parts = [quad_mesh(0.1 * box[1], 0.0, box[0], 0.0, box[2])]
+        for _ in range(1 + i % 3):
+            Vp, Tp = (icosphere(1 + i % 2) if rng.uniform() < 0.6 else box_mesh())
+            c = np.array([rng.uniform(0.2, 0.8) * b for b in box])
+            parts.append(((Vp * rng.uniform(0.1, 0.3) * min(box)) @ random_rotation(rng).T + c, Tp))
+        V, T = merge(parts)
+        g = Grid(nx, ny, nz, (0.0, 0.0, 0.0), h)
+        pos, nrm = receivers_plane(0.1 * box[1], 0.0, box[0], 0.0, box[2], 8, 8)
+        out.append(Scene(f"small-batch{i}", V.astype(np.float32), T, g,
+                         RefineParams(mask_vox=3.0, rays_per_voxel=5 + i, max_ray_vox=6.0, beta_vox=1.0,
+                                      key=(0x51, 0x7), scene_id=100 + i),
+                         ShadowParams(steps=32, max_step_vox=2.0), jfa_steps(g, extra_one=bool(i % 2)), 1, pos,
+                         nrm))
+    return out

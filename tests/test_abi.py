@@ -149,3 +149,71 @@ def test_product_path_has_no_cpu_fallback():
             assert "import oracle" not in src and "from oracle" not in src, fn
     src = open(os.path.join(pkg_dir, "rtsdf.py")).read()
     assert "raise RtsdfError" in src
+
+
+def _batch_scene(nx, ny, nz, V=10, T=4, steps=(8, 4, 2, 1)):
+    from paper_2210_06160_gb300 import scenes
+    from paper_2210_06160_gb300.rtsdf import make_batch_scene
+    g = scenes.Grid(nx, ny, nz, (0.0, 0.0, 0.0), 0.1)
+    return make_batch_scene(g, V, T, steps, scenes.RefineParams())
+
+
+def test_batch_plan_layout_without_gpu(lib):
+    from paper_2210_06160_gb300.rtsdf import BatchBuffers, BatchLayout, BatchScene, BatchTuning
+    P = C.c_void_p
+    descs = [_batch_scene(32, 32, 32, 100, 50), _batch_scene(17, 9, 33, 7, 0, (16, 8, 4, 2, 1)),
+             _batch_scene(5, 5, 5, 3, 1, ())]
+    arr = (BatchScene * 3)(*descs)
+    plan = P()
+    assert lib.rtsdf_batch_plan_create(arr, 3, C.byref(plan)) == 0 and plan.value
+    try:
+        nvox = lib.rtsdf_batch_voxels(plan)
+        lays = []
+        for i in range(3):
+            L = BatchLayout()
+            assert lib.rtsdf_batch_layout_of(plan, i, C.byref(L)) == 0
+            lays.append(L)
+        assert lib.rtsdf_batch_layout_of(plan, 3, C.byref(BatchLayout())) == 1
+        assert [L.voxel_offset for L in lays] == [0, 32768, 32768 + 5056]          # multiples of 64
+        assert nvox == 32768 + 5056 + 128
+        assert [L.vertex_offset for L in lays] == [0, 100, 107]
+        assert [L.triangle_offset for L in lays] == [0, 50, 50]
+        assert all(L.bvh_offset % 256 == 0 for L in lays) and lays[1].bvh_offset > lays[0].bvh_offset
+        assert [L.flooded_in_b for L in lays] == [0, 1, 0]                        # nsteps parity
+        assert lib.rtsdf_batch_bvh_bytes(plan) >= lib.rtsdf_bvh_bytes(50) + lib.rtsdf_bvh_bytes(1)
+        ws = lib.rtsdf_batch_workspace(plan)
+        assert ws >= 8 * nvox
+        t = BatchTuning()
+        assert lib.rtsdf_batch_get_tuning(plan, C.byref(t)) == 0 and (t.brick_x, t.brick_y, t.brick_z) == (4, 4, 4)
+        for bad in (BatchTuning(4, 4, 2, 2, 1), BatchTuning(8, 4, 2, 3, 1), BatchTuning(16, 2, 2, 2, 7)):
+            assert lib.rtsdf_batch_set_tuning(plan, C.byref(bad)) == 1
+        assert lib.rtsdf_batch_set_tuning(plan, C.byref(BatchTuning(16, 2, 2, 4, 0))) == 0
+        # argument errors are found before anything is enqueued
+        B = BatchBuffers(FAKE, FAKE, FAKE, FAKE + 4096, FAKE, FAKE, lib.rtsdf_batch_bvh_bytes(plan), FAKE, FAKE,
+                         FAKE, FAKE, FAKE, ws - 1)
+        assert lib.rtsdf_batch_rebuild(plan, C.byref(B), 0, 0, None, None) == 2
+        B.ws_bytes = ws
+        B.buf_b = FAKE
+        assert lib.rtsdf_batch_rebuild(plan, C.byref(B), 0, 0, None, None) == 1    # aliased JFA buffers
+        B.buf_b = FAKE + 4096
+        B.sdf = FAKE + 4
+        assert lib.rtsdf_batch_rebuild(plan, C.byref(B), 0, 0, None, None) == 1    # misaligned grid
+        assert lib.rtsdf_batch_autotune(plan, C.byref(B), 0, None, None) == 1
+    finally:
+        lib.rtsdf_batch_plan_destroy(plan)
+
+
+def test_batch_plan_validation(lib):
+    from paper_2210_06160_gb300.rtsdf import BatchScene
+    P = C.c_void_p
+    plan = P()
+    ok = _batch_scene(8, 8, 8)
+    assert lib.rtsdf_batch_plan_create((BatchScene * 1)(ok), 0, C.byref(plan)) == 1
+    assert lib.rtsdf_batch_plan_create((BatchScene * 65)(*([ok] * 65)), 65, C.byref(plan)) == 1
+    for bad in (_batch_scene(0, 8, 8), _batch_scene(8, 1024, 8), _batch_scene(8, 8, 8, steps=(0,)),
+                _batch_scene(8, 8, 8, V=-1)):
+        assert lib.rtsdf_batch_plan_create((BatchScene * 2)(ok, bad), 2, C.byref(plan)) == 1
+    b = _batch_scene(8, 8, 8)
+    b.nsteps = 17
+    assert lib.rtsdf_batch_plan_create((BatchScene * 1)(b), 1, C.byref(plan)) == 1
+    lib.rtsdf_batch_plan_destroy(None)
