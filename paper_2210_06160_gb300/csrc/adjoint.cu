@@ -308,21 +308,85 @@ __device__ __forceinline__ float3 closest_point_bary(float3 p, float3 A, float3 
     return make_float3(a.x + ab.x * sv + ac.x * sw, a.y + ab.y * sv + ac.y * sw, a.z + ab.z * sv + ac.z * sw);
 }
 
-__device__ __forceinline__ void add_vertex_grad(float* __restrict__ d_verts, const int32_t* __restrict__ tris, int tri,
-                                                const float lam[3], float3 dir, float scale) {
+// Per-voxel contribution to the vertex gradient: triangle `tri` gets, at vertex m,
+// scale * lam[m] * dir (9 values, m-major).
+struct VoxGrad {
+    int32_t tri;  // -1: none
+    float v[9];
+};
+
+__device__ __forceinline__ void set_grad(VoxGrad& o, int tri, const float lam[3], float3 dir, float scale) {
+    o.tri = tri;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const int vid = __ldg(tris + 3 * (int64_t)tri + m);
         const float s = scale * lam[m];
-        if (s == 0.0f) continue;
-        atomicAdd(d_verts + 3 * (int64_t)vid + 0, s * dir.x);
-        atomicAdd(d_verts + 3 * (int64_t)vid + 1, s * dir.y);
-        atomicAdd(d_verts + 3 * (int64_t)vid + 2, s * dir.z);
+        o.v[3 * m + 0] = s * dir.x;
+        o.v[3 * m + 1] = s * dir.y;
+        o.v[3 * m + 2] = s * dir.z;
     }
 }
 
-// One thread per voxel (grid-stride): rebuilds the voxel's frozen source from the
-// forward's state and scatters gsdf(v) * d field(v) / d vertices.
+// The frozen source of voxel lin and gsdf(v) * d field(v) / d vertices (world units).
+__device__ __forceinline__ VoxGrad voxel_grad(const FieldArgs& a, int64_t lin, const int32_t* __restrict__ nearest,
+                                              const int32_t* __restrict__ rep_tri,
+                                              const uint32_t* __restrict__ front, const uint32_t* __restrict__ back,
+                                              const uint32_t* __restrict__ win_ray,
+                                              const int32_t* __restrict__ win_tri, const float* __restrict__ gsdf) {
+    VoxGrad o;
+    o.tri = -1;
+    const GridD& g = a.g;
+    const float gs = __ldg(gsdf + lin);
+    if (gs == 0.0f) return o;
+    const int32_t sd = __ldg(nearest + lin);
+    if (sd == RTSDF_EMPTY) return o;  // constant field value
+    const int si = sd & 1023, sj = (sd >> 10) & 1023, sk = (sd >> 20) & 1023;
+    const int32_t rep = __ldg(rep_tri + ((int64_t)sk * g.ny + sj) * g.nx + si);
+    float3 A, B, C;
+    if (rep < 0 || rep >= a.T || !load_tri(a.verts, a.V, a.tris, rep, g, A, B, C)) return o;
+    const int i = (int)(lin % g.nx), j = (int)((lin / g.nx) % g.ny), k = (int)(lin / ((int64_t)g.nx * g.ny));
+    const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
+    const int dx = i - si, dy = j - sj, dz = k - sk;
+    const bool masked = (float)(dx * dx + dy * dy + dz * dz) <= a.mask2;
+    float sg = 1.0f;
+    if (masked) {
+        const uint32_t fr = __ldg(front + lin), bk = __ldg(back + lin);
+        bool neg = bk > fr;
+        if (fr == bk && a.fallback) neg = dot3(sub3(p, A), cross3(sub3(B, A), sub3(C, A))) < 0.0f;
+        sg = neg ? -1.0f : 1.0f;
+    }
+    const uint32_t wr = masked ? __ldg(win_ray + lin) : 0xFFFFFFFFu;
+    float lam[3];
+    if (wr == 0xFFFFFFFFu) {
+        // coarse source: |q - p| (minus beta when unmasked, times the vote when masked)
+        const float3 qp = closest_point_bary(p, A, B, C, lam);
+        const float u = sqrtf(dot3(qp, qp));
+        if (!(u > 0.0f)) return o;
+        set_grad(o, rep, lam, qp, gs * sg * a.inv_h / u);
+        return o;
+    }
+    // refined source: the winning ray's hit on its triangle
+    const int32_t tri = __ldg(win_tri + lin);
+    float3 d;
+    if (tri < 0 || tri >= a.T || !sphere_dir((uint32_t)lin, wr, a.scene, a.k0, a.k1, d)) return o;
+    if (!load_tri(a.verts, a.V, a.tris, tri, g, A, B, C)) return o;
+    const float3 e1 = sub3(B, A), e2 = sub3(C, A), nn = cross3(e1, e2);
+    const float3 x0 = sub3(A, p);
+    const float dn = dot3(d, nn);
+    if (dn == 0.0f) return o;
+    const float t = dot3(x0, nn) / dn;
+    const float3 ap = make_float3(t * d.x - x0.x, t * d.y - x0.y, t * d.z - x0.z);
+    const float n2 = dot3(nn, nn);
+    lam[1] = dot3(cross3(ap, e2), nn) / n2;
+    lam[2] = dot3(cross3(e1, ap), nn) / n2;
+    lam[0] = 1.0f - lam[1] - lam[2];
+    set_grad(o, tri, lam, nn, gs * sg * a.inv_h / dn);
+    return o;
+}
+
+// One thread per voxel (block-strided, warp-uniform trip count): the voxel's
+// contribution, then a segmented warp reduction over runs of consecutive lanes with
+// the same triangle (neighbouring voxels mostly share their source triangle), and
+// one set of atomics per run instead of one per voxel.
 __global__ void __launch_bounds__(256) k_field_adjoint(FieldArgs a, const int32_t* __restrict__ nearest,
                                                        const int32_t* __restrict__ rep_tri,
                                                        const uint32_t* __restrict__ front,
@@ -331,54 +395,39 @@ __global__ void __launch_bounds__(256) k_field_adjoint(FieldArgs a, const int32_
                                                        const int32_t* __restrict__ win_tri,
                                                        const float* __restrict__ gsdf, float* __restrict__ d_verts) {
     const GridD& g = a.g;
+    const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-    for (int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lin < n;
-         lin += (int64_t)gridDim.x * blockDim.x) {
-        const float gs = __ldg(gsdf + lin);
-        if (gs == 0.0f) continue;
-        const int32_t sd = __ldg(nearest + lin);
-        if (sd == RTSDF_EMPTY) continue;  // constant field value
-        const int si = sd & 1023, sj = (sd >> 10) & 1023, sk = (sd >> 20) & 1023;
-        const int32_t rep = __ldg(rep_tri + ((int64_t)sk * g.ny + sj) * g.nx + si);
-        float3 A, B, C;
-        if (rep < 0 || rep >= a.T || !load_tri(a.verts, a.V, a.tris, rep, g, A, B, C)) continue;
-        const int i = (int)(lin % g.nx), j = (int)((lin / g.nx) % g.ny), k = (int)(lin / ((int64_t)g.nx * g.ny));
-        const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
-        const int dx = i - si, dy = j - sj, dz = k - sk;
-        const bool masked = (float)(dx * dx + dy * dy + dz * dz) <= a.mask2;
-        float sg = 1.0f;
-        if (masked) {
-            const uint32_t fr = __ldg(front + lin), bk = __ldg(back + lin);
-            bool neg = bk > fr;
-            if (fr == bk && a.fallback) neg = dot3(sub3(p, A), cross3(sub3(B, A), sub3(C, A))) < 0.0f;
-            sg = neg ? -1.0f : 1.0f;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lin = base + threadIdx.x;
+        VoxGrad o;
+        o.tri = -1;
+        if (lin < n) o = voxel_grad(a, lin, nearest, rep_tri, front, back, win_ray, win_tri, gsdf);
+        if (o.tri < 0) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) o.v[c] = 0.0f;
         }
-        const uint32_t wr = masked ? __ldg(win_ray + lin) : 0xFFFFFFFFu;
-        float lam[3];
-        if (wr == 0xFFFFFFFFu) {
-            // coarse source: |q - p| (minus beta when unmasked, times the vote when masked)
-            const float3 qp = closest_point_bary(p, A, B, C, lam);
-            const float u = sqrtf(dot3(qp, qp));
-            if (!(u > 0.0f)) continue;
-            const float s = gs * sg * a.inv_h / u;
-            add_vertex_grad(d_verts, a.tris, rep, lam, qp, s);
-        } else {
-            // refined source: the winning ray's hit on its triangle
-            const int32_t tri = __ldg(win_tri + lin);
-            float3 d;
-            if (tri < 0 || tri >= a.T || !sphere_dir((uint32_t)lin, wr, a.scene, a.k0, a.k1, d)) continue;
-            if (!load_tri(a.verts, a.V, a.tris, tri, g, A, B, C)) continue;
-            const float3 e1 = sub3(B, A), e2 = sub3(C, A), nn = cross3(e1, e2);
-            const float3 x0 = sub3(A, p);
-            const float dn = dot3(d, nn);
-            if (dn == 0.0f) continue;
-            const float t = dot3(x0, nn) / dn;
-            const float3 ap = make_float3(t * d.x - x0.x, t * d.y - x0.y, t * d.z - x0.z);
-            const float n2 = dot3(nn, nn);
-            lam[1] = dot3(cross3(ap, e2), nn) / n2;
-            lam[2] = dot3(cross3(e1, ap), nn) / n2;
-            lam[0] = 1.0f - lam[1] - lam[2];
-            add_vertex_grad(d_verts, a.tris, tri, lam, nn, gs * sg * a.inv_h / dn);
+        if (!__any_sync(0xffffffffu, o.tri >= 0)) continue;
+        // runs of equal triangle ids: heads, and the last lane of this lane's run
+        const int prev = __shfl_up_sync(0xffffffffu, o.tri, 1);
+        const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != o.tri);
+        const uint32_t later = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+        const int run_end = later ? __ffs(later) - 2 : 31;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                const float u = __shfl_down_sync(0xffffffffu, o.v[c], off);
+                if (lane + off <= run_end) o.v[c] += u;
+            }
+        }
+        if (o.tri >= 0 && ((heads >> lane) & 1u)) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int vid = __ldg(a.tris + 3 * (int64_t)o.tri + m);
+                atomicAdd(d_verts + 3 * (int64_t)vid + 0, o.v[3 * m + 0]);
+                atomicAdd(d_verts + 3 * (int64_t)vid + 1, o.v[3 * m + 1]);
+                atomicAdd(d_verts + 3 * (int64_t)vid + 2, o.v[3 * m + 2]);
+            }
         }
     }
 }

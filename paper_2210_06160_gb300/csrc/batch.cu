@@ -210,6 +210,7 @@ struct PassD {
 
 struct PassTable {
     int32_t n;
+    int32_t m20, m10;  // -2^20, -2^10 (see jfa_column_interior)
     PassD e[kMaxBatch];
 };
 
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kJX* kJY) k_bjfa_pass(const __grid_constant__ 
     const PassD& e = p.e[lo];
     const int local = b - e.block_start;
     jfa_column(e.in, e.out, e.nx, e.ny, e.nz, e.k, e.nchunk, local % e.gbx, (local / e.gbx) % e.gby,
-               local / (e.gbx * e.gby));
+               local / (e.gbx * e.gby), p.m20, p.m10);
 }
 
 // ------------------------------------------------------------------ coarse field + refine
@@ -440,6 +441,8 @@ rtsdf_status enqueue_jfa(const rtsdf_batch_plan& P, uint32_t* a, uint32_t* b, cu
     for (int p = 0; p < P.npasses; ++p) {
         PassTable pt;
         memset(&pt, 0, sizeof(pt));
+        pt.m20 = -(1 << 20);
+        pt.m10 = -(1 << 10);
         int32_t blocks = 0;
         for (int si = 0; si < P.S; ++si) {
             const rtsdf_batch_scene& sc = P.scenes[si];

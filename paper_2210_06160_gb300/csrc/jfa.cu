@@ -4,9 +4,10 @@
 
 namespace rtsdf {
 
+// m20 = -2^20 and m10 = -2^10 (see jfa_column_interior)
 __global__ void __launch_bounds__(kJX* kJY) k_jfa_pass(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                     int nx, int ny, int nz, int k, int nchunk) {
-    jfa_column(in, out, nx, ny, nz, k, nchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+                                                     int nx, int ny, int nz, int k, int nchunk, int m20, int m10) {
+    jfa_column(in, out, nx, ny, nz, k, nchunk, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
 }
 
 rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* steps, int32_t nsteps,
@@ -19,7 +20,7 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
         const int nq = (g.nz + k - 1) / k;
         const int nchunk = (nq + kChunk - 1) / kChunk;
         const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)(k * nchunk));
-        k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk);
+        k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, -(1 << 20), -(1 << 10));
         RTSDF_LAUNCHED();
         uint32_t* t = src; src = dst; dst = t;
     }

@@ -35,15 +35,74 @@ constexpr int kChunk = 16;        // outputs per column and block along z
 // z = rz + p*k stream past; each loaded tap is decoded once and offered to the
 // (up to) three outputs p-1, p, p+1 that read it, so every output voxel costs
 // nine tap loads instead of 27.  Output p is complete once plane p+1 is in.
-__device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int nx, int ny,
-                                           int nz, int k, int nchunk, int bx, int by, int bz) {
-    const int x = bx * kJX + threadIdx.x;
-    const int y = by * kJY + threadIdx.y;
-    const int rz = bz / nchunk, ch = bz - rz * nchunk;
-    const int nq = (nz - rz + k - 1) / k;  // planes of this residue class
-    const int q0 = ch * kChunk, q1 = min(nq, q0 + kChunk);
-    if (x >= nx || y >= ny || q0 >= q1) return;
-    const int64_t plane = (int64_t)nx * ny;
+//
+// Columns whose 3x3 tap columns lie inside the grid take a specialised path for
+// power-of-two offsets (offset K known at compile time, so the nine taps of a plane
+// are three row pointers with immediate offsets).  It folds the empty marker into
+// the arithmetic instead of branching on it: 0xFFFFFFFF decodes to the seed
+// (1023, 1023, 4095), whose squared distance from any voxel of a grid with
+// dimensions <= 1023 exceeds 3070^2 > 3 * 1023^2, more than any real seed's, so it
+// never wins against one and is the result (the empty marker) only when every tap
+// is empty.  The candidate (d', s) is one signed 64-bit key, d' in the high word,
+// so the lexicographic argmin is a 64-bit minimum.
+//
+// The pass is bound by the integer ALU pipe (compares, selects, shifts and masks
+// issue at half rate there), while multiply-adds go to the FMA pipe.  So the seed
+// is decoded with two shifts and two multiply-adds by the runtime constants
+// m20 = -2^20 and m10 = -2^10 (kernel arguments, so they stay multiply-adds)
+// instead of masks, and the squared distance is a chain of multiply-adds.
+template <int K>
+__device__ __forceinline__ void jfa_column_interior(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                    int nx, int64_t plane, int x, int y, int rz, int nq, int q0,
+                                                    int q1, int m20, int m10) {
+    const int m2x = -2 * x, m2y = -2 * y;
+    const int64_t step = (int64_t)K * plane;
+    const long long none = 0x7fffffffffffffffll;
+    long long a0 = none, a1 = none, a2 = none;  // outputs p-1, p, p+1
+    const uint32_t* r0 = in + (int64_t)(rz + (q0 - 1) * K) * plane + (int64_t)(y - K) * nx + x;
+    const uint32_t* r1 = r0 + (int64_t)K * nx;
+    const uint32_t* r2 = r1 + (int64_t)K * nx;
+    for (int p = q0 - 1; p <= q1; ++p) {
+        if (p >= 0 && p < nq) {
+            const int z = rz + p * K;
+            const int m2z_prev = -2 * (z - K), m2z = -2 * z, m2z_next = -2 * (z + K);
+            uint32_t t[9];
+            t[0] = __ldg(r0 - K); t[1] = __ldg(r0); t[2] = __ldg(r0 + K);
+            t[3] = __ldg(r1 - K); t[4] = __ldg(r1); t[5] = __ldg(r1 + K);
+            t[6] = __ldg(r2 - K); t[7] = __ldg(r2); t[8] = __ldg(r2 + K);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const uint32_t s = t[i];
+                const uint32_t uz = s >> 20;
+                const uint32_t r = uz * (uint32_t)m20 + s;  // s - sz * 2^20 (mod 2^32)
+                const uint32_t uy = r >> 10;
+                const int sx = (int)(uy * (uint32_t)m10 + r);  // r - sy * 2^10
+                const int sy = (int)uy, sz = (int)uz;
+                int dxy = sx * m2x;
+                dxy = sx * sx + dxy;
+                dxy = sy * m2y + dxy;
+                dxy = sy * sy + dxy;
+                dxy = sz * sz + dxy;
+                a0 = min(a0, (long long)(((unsigned long long)(uint32_t)(dxy + m2z_prev * sz) << 32) | s));
+                a1 = min(a1, (long long)(((unsigned long long)(uint32_t)(dxy + m2z * sz) << 32) | s));
+                a2 = min(a2, (long long)(((unsigned long long)(uint32_t)(dxy + m2z_next * sz) << 32) | s));
+            }
+        }
+        const int done = p - 1;
+        if (done >= q0 && done < q1) out[(int64_t)(rz + done * K) * plane + (int64_t)y * nx + x] = (uint32_t)a0;
+        a0 = a1;
+        a1 = a2;
+        a2 = none;
+        r0 += step;
+        r1 += step;
+        r2 += step;
+    }
+}
+
+// Any column, any offset: bounds-checked taps, empty taps skipped.
+__device__ __forceinline__ void jfa_column_generic(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                   int nx, int ny, int64_t plane, int k, int x, int y, int rz,
+                                                   int nq, int q0, int q1) {
     const int m2x = -2 * x, m2y = -2 * y;
     const int xl = x - k, xh = x + k, yl = y - k, yh = y + k;
     const bool okxl = xl >= 0, okxh = xh < nx, okyl = yl >= 0, okyh = yh < ny;
@@ -78,6 +137,30 @@ __device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint
         a1 = a2;
         a2 = none;
     }
+}
+
+#define RTSDF_JFA_CASES(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256)
+
+// One thread: output column (x, y) over a block of z-planes of one residue class mod k.
+__device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int nx, int ny,
+                                           int nz, int k, int nchunk, int bx, int by, int bz, int m20, int m10) {
+    const int x = bx * kJX + threadIdx.x;
+    const int y = by * kJY + threadIdx.y;
+    const int rz = bz / nchunk, ch = bz - rz * nchunk;
+    const int nq = (nz - rz + k - 1) / k;  // planes of this residue class
+    const int q0 = ch * kChunk, q1 = min(nq, q0 + kChunk);
+    if (x >= nx || y >= ny || q0 >= q1) return;
+    const int64_t plane = (int64_t)nx * ny;
+    if (x >= k && x + k < nx && y >= k && y + k < ny) {
+        switch (k) {
+#define RTSDF_JFA_ONE(K) \
+    case K: jfa_column_interior<K>(in, out, nx, plane, x, y, rz, nq, q0, q1, m20, m10); return;
+            RTSDF_JFA_CASES(RTSDF_JFA_ONE)
+#undef RTSDF_JFA_ONE
+            default: break;
+        }
+    }
+    jfa_column_generic(in, out, nx, ny, plane, k, x, y, rz, nq, q0, q1);
 }
 
 }  // namespace rtsdf

@@ -10,6 +10,11 @@ launch ends quickly while the kernel sees the benchmark's voxel size and scene.
     python -m paper_2210_06160_gb300.profile_cases shadow
         the 1920x1080 shadow raymarch of the room on its rebuilt 400x200x400
         field (only the field and the receivers stay resident)
+    python -m paper_2210_06160_gb300.profile_cases adjoint
+        the 128^3 differentiation workload: one tracked forward, then three
+        rtsdf_backward calls (65,536 samples, 512x512 shadow image)
+    python -m paper_2210_06160_gb300.profile_cases batch
+        the 48-scene batch (118.8 M voxels): two batched rebuilds
 """
 from __future__ import annotations
 
@@ -71,6 +76,35 @@ def case_shadow() -> None:
     print("shadow ok", float(vis.mean()))
 
 
+def case_adjoint() -> None:
+    ds = scenes.scene_diff()
+    sc = ds.scene
+    v, t = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda()
+    pts = torch.from_numpy(ds.pts).cuda()
+    pos, nrm = torch.from_numpy(sc.recv_pos).cuda(), torch.from_numpy(sc.recv_nrm).cuda()
+    P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), track=True)
+    rp, sp = rt.make_refine_params(sc.refine), rt.make_shadow_params(sc.shadow)
+    P.rebuild(v, t, sc.jfa_steps, rp)
+    ones_s = torch.ones(len(ds.pts), dtype=torch.float32, device="cuda")
+    ones_v = torch.ones(len(sc.recv_pos), dtype=torch.float32, device="cuda")
+    dv = torch.empty_like(v)
+    dl = torch.empty(3, dtype=torch.float32, device="cuda")
+    ws = torch.empty(rt.rtsdf_backward_workspace(P.g), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        rt.rtsdf_backward(P.g, v, t, P.nearest, P.rep_tri, P.front, P.back, P.win_ray, P.win_tri, rp, P.sdf, pts,
+                          ones_s, pos, nrm, sp, ones_v, dv, dl, ws)
+    torch.cuda.synchronize()
+    print("adjoint ok", float(dv.abs().sum()), dl.tolist())
+
+
+def case_batch() -> None:
+    B = rt.Batch(scenes.scene_batch())
+    for _ in range(2):
+        B.rebuild(0, False)
+    torch.cuda.synchronize()
+    print("batch ok", rt.counters_dict(B.counters))
+
+
 if __name__ == "__main__":
     build.build()
     which = sys.argv[1] if len(sys.argv) > 1 else "jfa"
@@ -78,6 +112,10 @@ if __name__ == "__main__":
         case_jfa()
     elif which == "shadow":
         case_shadow()
+    elif which == "adjoint":
+        case_adjoint()
+    elif which == "batch":
+        case_batch()
     elif which == "refine-subbox":
         case_refine_subbox(int(sys.argv[2]) if len(sys.argv) > 2 else 3)
     else:
