@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SDF rebuild ms/frame @400x200x400, GVoxel/s, %HBM roof; bwd+batch vs plain"
+JFA_ROOM_DRAM_BYTES_PER_FRAME = 2_206_969_088
 
 
 def parse():
@@ -454,9 +455,13 @@ def run_ours(args):
         hbm_peak, peak_src = 6800.0, "fallback"
     jfa_bytes = 8.0 * nvox * len(sc.jfa_steps)  # 4 B read + 4 B write per voxel per pass
     jfa_gbs = jfa_bytes / (stage["jfa"] * 1e-3) / 1e9
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the ten passes of one
+    # room frame, from one ncu capture of this kernel version
+    traffic = JFA_ROOM_DRAM_BYTES_PER_FRAME if args.workload == "room" else None
     roofline = {"kernel": "k_jfa_pass (all passes of a frame)", "bound": "hbm", "achieved": round(jfa_gbs, 1),
-                "peak": hbm_peak, "unit": "GB/s", "frac": round(jfa_gbs / hbm_peak, 4), "traffic": None,
-                "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes}
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(jfa_gbs / hbm_peak, 4), "traffic": traffic,
+                "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes,
+                "limit": "integer ALU and FMA-heavy pipes (half-rate), not HBM"}
 
     counters = rt.counters_dict(P.counters)
 
