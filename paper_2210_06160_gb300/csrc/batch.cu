@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(512) k_bresolve(const __grid_constant__ BatchT
 }
 
 template <int BX, int BY, int BZ>
-__global__ void __launch_bounds__(kRefineMaxThreads, 4) k_brefine(const __grid_constant__ BatchTable t, BatchGrids G,
+__global__ void __launch_bounds__(kRefineMaxThreads, kRefineWarpsPerSm * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t, BatchGrids G,
                                                                   uint32_t frame, int accumulate,
                                                                   const char* __restrict__ bvh,
                                                                   const unsigned long long* __restrict__ bmask,
@@ -534,8 +534,8 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
                                         (int)(sizeof(WarpSmem) * 4)));
         attr_set[dev] = true;
     }
-    // the same 16 resident warps per SM for every CTA size (shared memory bound)
-    k_brefine<BX, BY, BZ><<<num_sms() * (16 / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
+    // the same resident warps per SM for every CTA size (shared memory bound)
+    k_brefine<BX, BY, BZ><<<num_sms() * (kRefineWarpsPerSm / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
                                                                             static_cast<const char*>(B.bvh), bmask,
                                                                             blist, count, counters);
     RTSDF_LAUNCHED();

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __
 
 // Persistent: warps take bricks from the work list until it is exhausted.
 template <bool kTrack>
-__global__ void __launch_bounds__(kRefineThreads, 8) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefineThreads) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
                                                               const int32_t* __restrict__ nearest,
@@ -169,11 +169,11 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
         attr_set[dev][track] = true;
     }
     if (track)
-        k_refine<true><<<num_sms() * 8, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
+        k_refine<true><<<num_sms() * (kRefineWarpsPerSm * 32 / kRefineThreads), kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
                                                                  w.blist, w.count, dist_bits, front, back, sdf,
                                                                  counters, win_ray, win_tri);
     else
-        k_refine<false><<<num_sms() * 8, kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
+        k_refine<false><<<num_sms() * (kRefineWarpsPerSm * 32 / kRefineThreads), kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
                                                                   w.blist, w.count, dist_bits, front, back, sdf,
                                                                   counters, nullptr, nullptr);
     RTSDF_LAUNCHED();

@@ -11,13 +11,14 @@
 
 namespace rtsdf {
 
-constexpr int kListCap = 512;        // staged leaves per warp and round
+constexpr int kListCap = 256;        // staged leaves per warp and round
 constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
 constexpr int kNarrowMargin = 96;    // > depth of any tree the builder makes (30-bit codes + 32 index bits)
 constexpr int kRaysPerLane = 8;      // rays of a voxel per group (one lane per voxel)
-constexpr int kFilterBatch = 4;      // staged triangles filtered per enqueue
+constexpr int kFilterBatch = 2;      // staged triangles filtered per enqueue
 constexpr int kQueueCap = 32 + 32 * 8 * kFilterBatch;  // queued ray/triangle items per warp
 constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
+constexpr int kRefineWarpsPerSm = 20;                 // resident refine warps per SM (shared memory bound)
 
 template <int BX, int BY, int BZ>
 struct BrickShape {
@@ -215,7 +216,9 @@ struct WarpSmem {
     uint32_t queue[kQueueCap];      // (list index << 8) | (slot << 3) | ray
     int qn;                         // queued items
     float4 origin[32];              // voxel centres of the pass's slots
-    float4 dir[8][32];              // ray directions of the group, [ray][slot]
+    float dirx[8][32];              // ray directions of the group, [ray][slot]
+    float diry[8][32];
+    float dirz[8][32];
     unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
 };
 
@@ -224,8 +227,8 @@ struct WarpSmem {
 __device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
                                          float tmax) {
     const int c = (int)(item >> 8), slot = (int)((item >> 3) & 31u), r = (int)(item & 7u);
-    const float4 of = w.origin[slot], df = w.dir[r][slot];
-    const float3 o = make_float3(of.x, of.y, of.z), d = make_float3(df.x, df.y, df.z);
+    const float4 of = w.origin[slot];
+    const float3 o = make_float3(of.x, of.y, of.z), d = make_float3(w.dirx[r][slot], w.diry[r][slot], w.dirz[r][slot]);
     const BvhLeaf* L = leaves + w.list[c];
     const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
     const float3 A = make_float3(v0.x, v0.y, v0.z);
@@ -258,7 +261,10 @@ __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf
     const float4 pl = __ldg(&leaf->pln);
     const float rho = sph.w;
     const float rho2 = rho * rho;
-    const float thr = dd > 2.0f * rho2 ? __fsqrt_rn(dd - rho2) * 0.999999f - 1e-4f : -rho;
+    // v * rsqrt(v) is within a few ulp of sqrt(v) (a few 1e-7 relative), well inside the
+    // 1e-6 relative and 1e-4 absolute margins, so the threshold stays below the exact one
+    const float v2 = dd - rho2;
+    const float thr = dd > 2.0f * rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho;
     const float sd = pl.w - __fmaf_rn(pl.x, o.x, __fmaf_rn(pl.y, o.y, pl.z * o.z));
     const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
     const float asd = fabsf(sd);
@@ -355,7 +361,9 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                     else
                         ++n_fail;
                 }
-                w.dir[r][lane] = make_float4(dir[r].x, dir[r].y, dir[r].z, 0.f);
+                w.dirx[r][lane] = dir[r].x;
+                w.diry[r][lane] = dir[r].y;
+                w.dirz[r][lane] = dir[r].z;
                 w.key[r][lane] = ~0ull;
             }
             float2 dx2[kRaysPerLane / 2], dy2[kRaysPerLane / 2], dz2[kRaysPerLane / 2];
