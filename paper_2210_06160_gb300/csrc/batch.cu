@@ -271,7 +271,7 @@ template <int BX, int BY, int BZ>
 __global__ void __launch_bounds__(512) k_bresolve(const __grid_constant__ BatchTable t, BatchGrids G, uint32_t frame,
                                                   int accumulate, unsigned long long* __restrict__ bmask,
                                                   int32_t* __restrict__ blist, uint32_t* __restrict__ count) {
-    __shared__ unsigned long long smask[8];
+    __shared__ unsigned long long smask[kMaxBricksPerTile];
     const int si = RTSDF_FIND_SCENE(t, tile_start, blockIdx.x);
     const SceneD& S = t.s[si];
     const int local = blockIdx.x - S.tile_start;

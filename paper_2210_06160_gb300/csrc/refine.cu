@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __
                                                  unsigned long long* __restrict__ bmask,
                                                  int32_t* __restrict__ blist, uint32_t* __restrict__ count,
                                                  uint32_t* __restrict__ win_ray, int32_t* __restrict__ win_tri) {
-    __shared__ unsigned long long smask[8];
+    __shared__ unsigned long long smask[kMaxBricksPerTile];
     resolve_tile<kBX, kBY, kBZ>(a, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), nearest, rep_tri, dist_bits,
                                 front, back, sdf, bmask, blist, count, win_ray, win_tri, 0, smask);
 }

@@ -22,9 +22,9 @@ constexpr int kRefineWarpsPerSm = 20;                 // resident refine warps p
 
 template <int BX, int BY, int BZ>
 struct BrickShape {
-    static_assert(BX * BY * BZ == 64, "a brick holds 64 voxels");
+    static_assert(BX * BY * BZ == 64 || BX * BY * BZ == 32, "a brick holds 64 or 32 voxels");
     static_assert(32 % BX == 0 && 4 % BY == 0 && 4 % BZ == 0, "bricks tile the 32x4x4 resolve tile");
-    static constexpr int kPerTile = (32 / BX) * (4 / BY) * (4 / BZ);  // = 8
+    static constexpr int kPerTile = (32 / BX) * (4 / BY) * (4 / BZ);  // 8 or 16
 };
 
 struct RefineArgs {
@@ -43,6 +43,8 @@ struct RefineArgs {
     int nbx, nby, nbz;  // brick grid
 };
 
+constexpr int kMaxBricksPerTile = 16;
+
 // One 32x4x4 tile of voxels (512 threads, tile coordinates tb): coarse distance u_c
 // to the representative triangle of the flooded seed; unmasked voxels get their
 // final value (u_c - beta); masked voxels initialise their refine state (and, when
@@ -57,10 +59,10 @@ __device__ __forceinline__ void resolve_tile(const RefineArgs& a, int3 tb, const
                                              int32_t* __restrict__ blist, uint32_t* __restrict__ count,
                                              uint32_t* __restrict__ win_ray, int32_t* __restrict__ win_tri,
                                              int32_t tag, unsigned long long* smask) {
-    constexpr int kBpx = 32 / BX, kBpy = 4 / BY;
+    constexpr int kBpx = 32 / BX, kBpy = 4 / BY, kPer = BrickShape<BX, BY, BZ>::kPerTile;
     const int tx = threadIdx.x & 31, ty = (threadIdx.x >> 5) & 3, tz = threadIdx.x >> 7;
     const int i = tb.x * 32 + tx, j = tb.y * 4 + ty, k = tb.z * 4 + tz;
-    if (threadIdx.x < 8) smask[threadIdx.x] = 0ull;
+    if (threadIdx.x < kPer) smask[threadIdx.x] = 0ull;
     __syncthreads();
     bool masked = false;
     if (i < a.g.nx && j < a.g.ny && k < a.g.nz) {
@@ -120,7 +122,7 @@ __device__ __forceinline__ void resolve_tile(const RefineArgs& a, int3 tb, const
         const int lb = threadIdx.x;
         const int bx = tb.x * kBpx + lb % kBpx, by = tb.y * kBpy + (lb / kBpx) % kBpy,
                   bz = tb.z * (4 / BZ) + lb / (kBpx * kBpy);
-        const bool valid = lb < 8 && bx < a.nbx && by < a.nby && bz < a.nbz;
+        const bool valid = lb < kPer && bx < a.nbx && by < a.nby && bz < a.nbz;
         const unsigned long long m = valid ? smask[lb] : 0ull;
         const int64_t b = ((int64_t)bz * a.nby + by) * a.nbx + bx;
         if (valid) bmask[b] = m;
@@ -247,9 +249,11 @@ __device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict_
 // pair must be within reach of the bounding sphere; each ray's line must pass
 // within rho of the sphere centre with the centre at most rho behind the origin
 // (off the rho-sphere by more than rho*sqrt(2) that is exactly tc >= sqrt(dd -
-// rho^2); nearer, tc >= -rho is kept, a superset); and the ray must head for the
-// triangle's plane and cross it within the ray length.  All margins exceed the
-// FP32 rounding of both sides, so no triangle the exact test accepts is dropped.
+// rho^2); nearer, tc >= -rho is kept, a superset); and the ray must cross the
+// triangle's plane at a parameter t_p = sd / dn in [0, tmax], written without a
+// division as |sd - h dn| <= h |dn| (h = tmax / 2) and widened by eps in sd.  All
+// margins exceed the FP32 rounding of both sides, so no triangle the exact test
+// accepts is dropped.
 __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf, float3 o, uint32_t okm,
                                                 const float2* dx2, const float2* dy2, const float2* dz2,
                                                 float tmax) {
@@ -267,16 +271,18 @@ __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf
     const float thr = dd > 2.0f * rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho;
     const float sd = pl.w - __fmaf_rn(pl.x, o.x, __fmaf_rn(pl.y, o.y, pl.z * o.z));
     const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
-    const float asd = fabsf(sd);
+    const float h = 0.5f * tmax;
     const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
     const float2 nx2 = make_float2(pl.x, pl.x), ny2 = make_float2(pl.y, pl.y), nz2 = make_float2(pl.z, pl.z);
+    const float2 sd2 = make_float2(sd, sd), mh2 = make_float2(-h, -h);
     uint32_t pm = 0;
 #pragma unroll
     for (int r = 0; r < kRaysPerLane / 2; ++r) {
         const float2 tc = __ffma2_rn(cx2, dx2[r], __ffma2_rn(cy2, dy2[r], __fmul2_rn(cz2, dz2[r])));
         const float2 dn = __ffma2_rn(nx2, dx2[r], __ffma2_rn(ny2, dy2[r], __fmul2_rn(nz2, dz2[r])));
-        const bool ok0 = tc.x >= thr && sd * dn.x > -eps && asd <= __fmaf_rn(tmax, fabsf(dn.x), eps);
-        const bool ok1 = tc.y >= thr && sd * dn.y > -eps && asd <= __fmaf_rn(tmax, fabsf(dn.y), eps);
+        const float2 u = __ffma2_rn(mh2, dn, sd2);  // sd - h dn
+        const bool ok0 = tc.x >= thr && fabsf(u.x) <= __fmaf_rn(h, fabsf(dn.x), eps);
+        const bool ok1 = tc.y >= thr && fabsf(u.y) <= __fmaf_rn(h, fabsf(dn.y), eps);
         pm |= ((ok0 ? 1u : 0u) << (2 * r)) | ((ok1 ? 1u : 0u) << (2 * r + 1));
     }
     return pm & okm;
