@@ -188,6 +188,54 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU path
 
+def bench_dynamic(dev, frames: int = 120, warmup: int = 3) -> dict:
+    """The room animated over `frames` frames (seeded linear and angular motion, 10
+    deforming primitives): every frame re-voxelizes, rebuilds the BVH, floods and refines
+    with 4 rays per voxel, then shades 1920x1080 receivers. Per-frame vertex arrays
+    are uploaded before timing; each frame is timed with events. Run twice: fresh per
+    frame (no carry-over) and with the Eq. (1) decay (alpha 0.95)."""
+    import numpy as np
+    import torch
+
+    from paper_2210_06160_gb300 import rtsdf as rt
+    from paper_2210_06160_gb300 import scenes
+
+    anim = scenes.room_animation()
+    sc = anim.scene
+    verts = [torch.from_numpy(scenes.room_frame(anim, f)).to(dev) for f in range(frames)]
+    tris = torch.from_numpy(sc.tris).to(dev)
+    pos = torch.from_numpy(sc.recv_pos).to(dev)
+    nrm = torch.from_numpy(sc.recv_nrm).to(dev)
+    P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), device=dev)
+    vis = torch.empty(len(sc.recv_pos), dtype=torch.float32, device=dev)
+    sp = rt.make_shadow_params(sc.shadow)
+    stream = torch.cuda.current_stream()
+    out = {"workload": (f"room 400x200x400 animated, {frames} frames, {len(sc.tris)} triangles, "
+                        f"{sc.refine.rays_per_voxel} rays/voxel, full rebuild + 1920x1080 shadow per frame")}
+    for label, mode in (("fresh", 0), ("decay", 2)):
+        def frame(f):
+            rp = rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f,
+                                                           accumulate=mode if f > 0 else 0))
+            P.rebuild(verts[f], tris, sc.jfa_steps, rp)
+            P.shadow(pos, nrm, sp, vis)
+
+        for f in range(warmup):
+            frame(f)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+        for f in range(frames):
+            evs[f][0].record(stream)
+            frame(f)
+            evs[f][1].record(stream)
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in evs])
+        out[label] = {"p50_ms": round(float(np.percentile(ms, 50)), 4), "p99_ms": round(float(np.percentile(ms, 99)), 4),
+                      "mean_ms": round(float(ms.mean()), 4), "max_ms": round(float(ms.max()), 4)}
+    del P, verts
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batch(dev, steps: int = 5, warmup: int = 2) -> dict:
     """48 seeded scenes of uneven sizes (dims from 32^3 .. 256x128x256, 500-60k
     triangles, 8 rays/voxel): one batched rebuild (voxelize + BVH + JFA + refine,
@@ -503,10 +551,11 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h_verts.numel() * 4 + h_tris.numel() * 4),
                "d2h_bytes_per_step": int(h_sdf.numel() * 4 + h_vis.numel() * 4), "steps": ke}
 
-    bwd = batch = None
+    bwd = batch = dyn = None
     if args.workload == "room" and not args.no_extensions:
         bwd = bench_backward(dev)
         batch = bench_batch(dev)
+        dyn = bench_dynamic(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -521,7 +570,7 @@ def run_ours(args):
                 "rebuild_ms": round(rebuild_ms, 4),
                 "stage_ms": {k: round(v, 4) for k, v in stage.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "backward": bwd, "batch": batch,
+                "backward": bwd, "batch": batch, "dynamic": dyn,
                 "clocks": clk, "counters": counters, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -70,8 +70,10 @@ typedef struct {
     uint32_t key[2];        /* Philox4x32-10 key */
     uint32_t frame_index;   /* ray r of this call has ray id frame_index*R + r */
     uint32_t scene_id;      /* third Philox counter word */
-    int32_t accumulate;     /* 1: keep dist/front/back of earlier frames (Sec. 2.1 temporal accumulation) */
+    int32_t accumulate;     /* 0: fresh; 1: keep the minimum and the votes of earlier frames (Sec. 2.1
+                               temporal accumulation); 2: decayed accumulation of Eq. (1), see rtsdf_refine */
     int32_t sign_fallback;  /* 1: front == back -> side of the representative triangle's plane */
+    float decay_alpha;      /* alpha of Eq. (1) (accumulate = 2), in [0, 1] */
 } rtsdf_refine_params;
 
 /* Soft-shadow raymarch (Sec. 2.4, 2.5.2, 2.5.3); distances in voxels. */
@@ -180,9 +182,12 @@ size_t rtsdf_refine_workspace(const rtsdf_grid* g);
  *    scene_id, attempt) + Marsaglia's rejection method).  The closest hit of each
  *    ray (0 < t <= max_ray_vox, ties -> lower triangle id) lowers dist and adds a
  *    front (ray meets the counter-clockwise side) or back vote.
- *  - State: dist_bits (float bits), front, back are nx*ny*nz uint32, defined at
- *    masked voxels.  accumulate = 0 starts them at (u_c, 0, 0); accumulate = 1
- *    keeps earlier frames (dist = min(dist, u_c)).
+ *  - State: dist_bits (float bits), front, back are nx*ny*nz uint32.  Unmasked
+ *    voxels get (u_c, 0, 0).  At masked voxels accumulate = 0 starts them at
+ *    (u_c, 0, 0); accumulate = 1 keeps earlier frames (dist = min(dist, u_c), votes
+ *    kept); accumulate = 2 is Eq. (1) (Sec. 2.5.1): dist = alpha * f + (1 - alpha) *
+ *    u_c with f the previous frame's dist, then the minimum with this frame's hits;
+ *    votes are this frame's only.
  *  - sdf_out (nx*ny*nz float) at masked voxels: -dist if back > front, +dist if
  *    front > back; on a tie the side of rep_tri's plane when sign_fallback, else +.
  * verts/tris must be the mesh the BVH and rep_tri were built from. */
@@ -346,7 +351,8 @@ rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_plan* plan, const rtsdf_batch_tu
 
 /* One frame of every scene: voxelize, BVH, JFA (each scene's own steps, aligned so
  * that all scenes end on the last pass), coarse field and ray mask, refinement with
- * ray ids frame_index*R + r and the given accumulate flag.  counters may be NULL
+ * ray ids frame_index*R + r and the given accumulate mode (0, 1, 2 as in
+ * rtsdf_refine_params; mode 2 takes each scene's decay_alpha).  counters may be NULL
  * (batch totals).  If the JFA graph is used, the first call with a given pair of
  * JFA buffers captures it (on a stream of the plan) and later calls replay it. */
 rtsdf_status rtsdf_batch_rebuild(rtsdf_batch_plan* plan, const rtsdf_batch_buffers* b, uint32_t frame_index,

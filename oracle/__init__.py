@@ -233,17 +233,30 @@ def shadow(grid, sdf, pos, nrm, sp) -> np.ndarray:
     return vis
 
 
-def init_refine_state(u_c, mask, state=None, accumulate=False):
+def init_refine_state(u_c, mask, state=None, accumulate=0, alpha=0.95):
     """Refinement state before a frame's rays: masked voxels start from the coarse
     distance (or the smaller of it and the accumulated distance), counts from zero
     (or the accumulated counts); unmasked voxels hold the coarse distance, no votes.
     With a 5-tuple state (dist, front, back, win_ray, win_tri) the winner record
-    follows: the coarse source wins when it sets the distance."""
+    follows: the coarse source wins when it sets the distance.
+
+    accumulate = 2 is the decayed accumulation of Sec. 2.5.1, Eq. (1): masked voxels
+    start from alpha * f_{t-1} + (1 - alpha) * c_t (FP32, products then sum; c_t the
+    coarse distance), which this frame's hits then lower (the minimum with r_t);
+    votes are this frame's only; unmasked voxels take c_t."""
     d0 = u_c.view(np.uint32).copy()
     none_ray = np.full_like(d0, 0xFFFFFFFF)
     none_tri = np.full(d0.shape, -1, dtype=np.int32)
     if state is None or not accumulate:
         return d0, np.zeros_like(d0), np.zeros_like(d0), none_ray, none_tri
+    if int(accumulate) == 2:
+        m = mask.astype(bool)
+        a = np.float32(alpha)
+        f_prev = np.ascontiguousarray(state[0], dtype=np.uint32).view(np.float32)
+        blend = (a * f_prev + (np.float32(1.0) - a) * u_c.astype(np.float32)).astype(np.float32)
+        dist = np.where(m, blend.view(np.uint32), d0).astype(np.uint32)
+        zeros = np.zeros_like(d0)
+        return np.ascontiguousarray(dist), zeros, zeros.copy(), none_ray, none_tri
     dist, fr, bk = state[:3]
     wr = state[3] if len(state) > 3 else none_ray
     wt = state[4] if len(state) > 4 else none_tri
@@ -272,7 +285,7 @@ def rebuild(scene, frames: int | None = None, frame0: int = 0, voxel_subset=None
     state = None
     nf = scene.frames if frames is None else frames
     for f in range(nf):
-        state = init_refine_state(u_c, mask, state, accumulate=rp.accumulate)
+        state = init_refine_state(u_c, mask, state, accumulate=rp.accumulate, alpha=rp.decay_alpha)
         dist, fr, bk, wr, wt = (a.ravel() for a in state)
         refine_voxels(g, vv, scene.tris, todo, rp, frame0 + f, dist, fr, bk, wr, wt)
         state = tuple(a.reshape(g.shape_zyx) for a in (dist, fr, bk, wr, wt))

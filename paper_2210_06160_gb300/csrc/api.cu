@@ -106,6 +106,8 @@ rtsdf_status refine_checked(const rtsdf_grid* g, const float* verts, int32_t V, 
         return RTSDF_EINVAL;
     if (counters && !aligned(counters, 4)) return RTSDF_EINVAL;
     if (p->rays_per_voxel < 1 || p->rays_per_voxel > 4096) return RTSDF_EINVAL;
+    if (p->accumulate < 0 || p->accumulate > 2) return RTSDF_EINVAL;
+    if (p->accumulate == 2 && !(p->decay_alpha >= 0.0f && p->decay_alpha <= 1.0f)) return RTSDF_EINVAL;
     if (!(p->mask_vox >= 0.0f) || !isfinite(p->mask_vox) || !(p->max_ray_vox > 0.0f) || !isfinite(p->beta_vox))
         return RTSDF_EINVAL;
     if (bvh_bytes_ < bvh_bytes(T)) return RTSDF_ENOMEM;

@@ -39,7 +39,7 @@ struct SceneD {
     int64_t vox_off, bvh_off, brick_off;
     int32_t tile_start;  // first 32x4x4 resolve tile of the scene in the batch
     int32_t flood_b;     // flooded seeds in buffer b
-    float mask2, beta, empty_dist, tmax;
+    float mask2, beta, empty_dist, tmax, alpha;
     int32_t R, fallback;
     uint32_t k0, k1, scene;
     int32_t pad;
@@ -249,6 +249,8 @@ __device__ __forceinline__ RefineArgs scene_args(const SceneD& S, const float* v
     a.scene = S.scene;
     a.accumulate = accumulate;
     a.fallback = S.fallback;
+    a.alpha = S.alpha;
+    a.one_minus_alpha = 1.0f - S.alpha;
     a.nbx = (S.g.nx + BX - 1) / BX;
     a.nby = (S.g.ny + BY - 1) / BY;
     a.nbz = (S.g.nz + BZ - 1) / BZ;
@@ -424,6 +426,7 @@ BatchTable make_table(const rtsdf_batch_plan& P, const Shape& sh) {
         d.beta = sc.refine.beta_vox;
         d.empty_dist = (float)(sc.grid.nx + sc.grid.ny + sc.grid.nz);
         d.tmax = sc.refine.max_ray_vox;
+        d.alpha = sc.refine.decay_alpha;
         d.R = sc.refine.rays_per_voxel;
         d.fallback = sc.refine.sign_fallback;
         d.k0 = sc.refine.key[0];
@@ -751,7 +754,11 @@ rtsdf_status rtsdf_batch_rebuild(rtsdf_batch_plan* plan, const rtsdf_batch_buffe
                                  int32_t accumulate, rtsdf_counters* counters, rtsdf_stream stream) {
     RTSDF_TRY(buffers_ok(plan, b));
     if (counters && reinterpret_cast<uintptr_t>(counters) % 4) return RTSDF_EINVAL;
-    return rebuild(*plan, *b, frame_index, accumulate ? 1 : 0, counters, cs(stream));
+    if (accumulate < 0 || accumulate > 2) return RTSDF_EINVAL;
+    if (accumulate == 2)
+        for (const rtsdf_batch_scene& sc : plan->scenes)
+            if (!(sc.refine.decay_alpha >= 0.0f && sc.refine.decay_alpha <= 1.0f)) return RTSDF_EINVAL;
+    return rebuild(*plan, *b, frame_index, accumulate, counters, cs(stream));
 }
 
 rtsdf_status rtsdf_batch_autotune(rtsdf_batch_plan* plan, const rtsdf_batch_buffers* b, int32_t reps,

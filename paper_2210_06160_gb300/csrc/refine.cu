@@ -144,6 +144,8 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
     a.frame = p.frame_index;
     a.scene = p.scene_id;
     a.accumulate = p.accumulate;
+    a.alpha = p.decay_alpha;
+    a.one_minus_alpha = 1.0f - p.decay_alpha;
     a.fallback = p.sign_fallback;
     a.nbx = (gh.nx + kBX - 1) / kBX;
     a.nby = (gh.ny + kBY - 1) / kBY;

@@ -40,6 +40,7 @@ struct RefineArgs {
     float tmax;
     uint32_t k0, k1, frame, scene;
     int accumulate, fallback;
+    float alpha, one_minus_alpha;  // Eq. (1) decay (accumulate = 2)
     int nbx, nby, nbz;  // brick grid
 };
 
@@ -47,8 +48,9 @@ constexpr int kMaxBricksPerTile = 16;
 
 // One 32x4x4 tile of voxels (512 threads, tile coordinates tb): coarse distance u_c
 // to the representative triangle of the flooded seed; unmasked voxels get their
-// final value (u_c - beta); masked voxels initialise their refine state (and, when
-// tracked, the coarse source takes the winner record where it sets the distance).
+// final value (u_c - beta) and the state (u_c, 0, 0); masked voxels initialise their
+// refine state (and, when tracked, the coarse source takes the winner record where
+// it sets the distance).
 // The tile's bricks get 64-bit masks of their masked voxels from warp ballots, and
 // bricks with any masked voxel are appended to the work list as (tag | brick).
 template <int BX, int BY, int BZ>
@@ -87,19 +89,23 @@ __device__ __forceinline__ void resolve_tile(const RefineArgs& a, int3 tb, const
         // winner record (tracked calls): the coarse source holds a voxel's distance
         // when the voxel is unmasked, starts fresh, or its coarse distance is lower
         bool coarse_wins = true;
+        const uint32_t ub = __float_as_uint(uc);
         if (!masked) {
             sdf[lin] = uc - a.beta;
+            dist_bits[lin] = ub;
+            front[lin] = 0u;
+            back[lin] = 0u;
+        } else if (a.accumulate == 1) {
+            const uint32_t old = dist_bits[lin];
+            coarse_wins = ub < old;
+            dist_bits[lin] = min(old, ub);
         } else {
-            const uint32_t ub = __float_as_uint(uc);
-            if (a.accumulate) {
-                const uint32_t old = dist_bits[lin];
-                coarse_wins = ub < old;
-                dist_bits[lin] = min(old, ub);
-            } else {
-                dist_bits[lin] = ub;
-                front[lin] = 0u;
-                back[lin] = 0u;
-            }
+            // fresh, or Eq. (1): alpha * f_{t-1} + (1 - alpha) * c_t before this frame's hits
+            const float f = a.accumulate == 2 ? a.alpha * __uint_as_float(dist_bits[lin]) + a.one_minus_alpha * uc
+                                              : uc;
+            dist_bits[lin] = __float_as_uint(f);
+            front[lin] = 0u;
+            back[lin] = 0u;
         }
         if (win_ray && coarse_wins) {
             win_ray[lin] = 0xFFFFFFFFu;

@@ -36,7 +36,8 @@ class Grid(C.Structure):
 class RefineParams(C.Structure):
     _fields_ = [("mask_vox", C.c_float), ("rays_per_voxel", C.c_int32), ("max_ray_vox", C.c_float),
                 ("beta_vox", C.c_float), ("key", C.c_uint32 * 2), ("frame_index", C.c_uint32),
-                ("scene_id", C.c_uint32), ("accumulate", C.c_int32), ("sign_fallback", C.c_int32)]
+                ("scene_id", C.c_uint32), ("accumulate", C.c_int32), ("sign_fallback", C.c_int32),
+                ("decay_alpha", C.c_float)]
 
 
 class ShadowParams(C.Structure):
@@ -164,7 +165,8 @@ def make_grid(g) -> Grid:
 def make_refine_params(rp) -> RefineParams:
     return RefineParams(float(rp.mask_vox), int(rp.rays_per_voxel), float(rp.max_ray_vox), float(rp.beta_vox),
                         (C.c_uint32 * 2)(*[int(k) & 0xFFFFFFFF for k in rp.key]), int(rp.frame_index) & 0xFFFFFFFF,
-                        int(rp.scene_id) & 0xFFFFFFFF, int(bool(rp.accumulate)), int(bool(rp.sign_fallback)))
+                        int(rp.scene_id) & 0xFFFFFFFF, int(rp.accumulate), int(bool(rp.sign_fallback)),
+                        float(getattr(rp, "decay_alpha", 0.95)))
 
 
 def make_shadow_params(sp) -> ShadowParams:
@@ -455,7 +457,7 @@ def rtsdf_batch_plan_create(scenes: list) -> C.c_void_p:
 
 def rtsdf_batch_rebuild(plan, buffers: BatchBuffers, frame_index: int, accumulate: bool, counters=None,
                         stream=None) -> None:
-    _check(lib().rtsdf_batch_rebuild(plan, C.byref(buffers), int(frame_index) & 0xFFFFFFFF, int(bool(accumulate)),
+    _check(lib().rtsdf_batch_rebuild(plan, C.byref(buffers), int(frame_index) & 0xFFFFFFFF, int(accumulate),
                                      _dev(counters, torch.int32, "counters"), _stream(stream)), "rtsdf_batch_rebuild")
 
 

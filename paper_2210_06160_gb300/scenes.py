@@ -174,8 +174,9 @@ class RefineParams:
     key: tuple[int, int] = (0, 0)  # counter-based generator key
     frame_index: int = 0
     scene_id: int = 0
-    accumulate: bool = False
+    accumulate: int = 0            # 0 fresh, 1 min-accumulate (bool True), 2 decay of Eq. (1)
     sign_fallback: bool = True
+    decay_alpha: float = 0.95      # Eq. (1) alpha (Sec. 2.5.1)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -257,10 +258,12 @@ def _prim(kind: str) -> tuple[np.ndarray, np.ndarray]:
 
 def room_primitives(rng: np.random.Generator, count: int, box: tuple[float, float, float],
                     target_tris: int | None, tol: float = 0.10,
-                    scale=(0.05, 0.3)) -> list[tuple[np.ndarray, np.ndarray]]:
+                    scale=(0.05, 0.3), poses: list | None = None) -> list[tuple[np.ndarray, np.ndarray]]:
     """`count` seeded primitives (icosphere s4 / box / torus 64x32) with random pose and scale.
 
     When `target_tris` is given, primitive types are redrawn until the total is within `tol`.
+    When `poses` is a list, (unit mesh V, T, centre, scale, rotation) of every primitive
+    is appended to it.
     """
     kinds = ("sphere", "box", "torus")
     sizes = {k: len(_prim(k)[1]) for k in kinds}
@@ -277,6 +280,8 @@ def room_primitives(rng: np.random.Generator, count: int, box: tuple[float, floa
         s = rng.uniform(*scale)
         R = random_rotation(rng)
         parts.append(((V * s) @ R.T + c, T))
+        if poses is not None:
+            poses.append((V, T, c, s, R))
     return parts
 
 
@@ -425,3 +430,87 @@ def scene_batch_small(seed: int = 77) -> list[Scene]:
                          ShadowParams(steps=32, max_step_vox=2.0), jfa_steps(g, extra_one=bool(i % 2)), 1, pos,
                          nrm))
     return out
+
+
+def _axis_angle(w: np.ndarray) -> np.ndarray:
+    """Rotation matrix of the rotation vector w (Rodrigues)."""
+    th = float(np.linalg.norm(w))
+    if th == 0.0:
+        return np.eye(3)
+    k = w / th
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * (K @ K)
+
+
+def _vertex_normals(V: np.ndarray, T: np.ndarray) -> np.ndarray:
+    fn = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    vn = np.zeros_like(V)
+    for m in range(3):
+        np.add.at(vn, T[:, m], fn)
+    return vn / np.maximum(np.linalg.norm(vn, axis=1, keepdims=True), 1e-30)
+
+
+@dataclasses.dataclass
+class RoomAnimation:
+    """The room scene set in motion: per primitive a seeded linear velocity (|v| <= vmax
+    per frame, reflected at the walls) and angular velocity (<= wmax per frame); `ndeform`
+    primitives also move every vertex along its rest normal by amp * sin(2 pi f / 60 + phase)."""
+    scene: Scene                 # frame 0 (geometry, grid, parameters, receivers)
+    ground: np.ndarray           # ground quad vertices
+    poses: list                  # (unit V, T, centre, scale, rotation) per primitive
+    vel: np.ndarray
+    omega: np.ndarray
+    deform: dict                 # primitive index -> (rest normals, phases)
+    box: tuple
+    amp: float
+
+
+def room_animation(seed: int = 2210, nx: int = 400, ny: int = 200, nz: int = 400, n_prims: int = 40,
+                   target_tris: int = 100_000, shadow_w: int = 1920, shadow_h: int = 1080, rays: int = 4,
+                   vmax: float = 0.005, wmax_deg: float = 2.0, ndeform: int = 10, amp: float = 0.02,
+                   motion_seed: int = 120) -> RoomAnimation:
+    """The dynamic workload: the room of scene_room (same seed, so frame 0 is that scene)
+    rebuilt every frame from scratch with `rays` rays per voxel and no carry-over."""
+    rng = np.random.default_rng(seed)
+    box = (2.0, 1.0, 2.0)
+    h = box[0] / nx
+    ground = quad_mesh(0.05, 0.0, 2.0, 0.0, 2.0)
+    poses: list = []
+    parts = [ground] + room_primitives(rng, n_prims, box, target_tris, poses=poses)
+    V, T = merge(parts)
+    g = Grid(nx, ny, nz, (0.0, 0.0, 0.0), h)
+    pos, nrm = receivers_plane(0.05, 0.0, 2.0, 0.0, 2.0, shadow_w, shadow_h)
+    sc = Scene(f"dynamic-room-{nx}x{ny}x{nz}", V.astype(np.float32), T, g,
+               RefineParams(mask_vox=4.0, rays_per_voxel=rays, max_ray_vox=8.0, beta_vox=1.0, accumulate=False),
+               ShadowParams(steps=96, max_step_vox=0.05 / h), jfa_steps(g, extra_one=True), 1, pos, nrm)
+    mr = np.random.default_rng(motion_seed)
+    n = len(poses)
+    dirs = mr.normal(size=(n, 3))
+    vel = dirs / np.linalg.norm(dirs, axis=1, keepdims=True) * mr.uniform(0, vmax, (n, 1))
+    axes = mr.normal(size=(n, 3))
+    omega = axes / np.linalg.norm(axes, axis=1, keepdims=True) * np.radians(mr.uniform(0, wmax_deg, (n, 1)))
+    deform = {}
+    for i in sorted(mr.choice(n, min(ndeform, n), replace=False).tolist()):
+        Vu, Tu = poses[i][0], poses[i][1]
+        deform[i] = (_vertex_normals(Vu, Tu), mr.uniform(0, 2 * math.pi, len(Vu)))
+    return RoomAnimation(sc, ground[0], poses, vel, omega, deform, box, amp)
+
+
+def _reflect(x: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    span = hi - lo
+    y = np.mod(x - lo, 2 * span)
+    return lo + np.where(y > span, 2 * span - y, y)
+
+
+def room_frame(anim: RoomAnimation, f: int) -> np.ndarray:
+    """World vertices of frame f (same triangles as anim.scene)."""
+    out = [anim.ground]
+    for i, (Vu, Tu, c, s, R) in enumerate(anim.poses):
+        Vl = Vu
+        if i in anim.deform:
+            vn, ph = anim.deform[i]
+            Vl = Vu + (anim.amp / s) * np.sin(2 * math.pi * f / 60.0 + ph)[:, None] * vn
+        Rf = _axis_angle(anim.omega[i] * f) @ R
+        cf = np.array([_reflect(np.array(c[a] + anim.vel[i, a] * f), 0.1, anim.box[a] - 0.1) for a in range(3)])
+        out.append((Vl * s) @ Rf.T + cf)
+    return np.concatenate(out).astype(np.float32)

@@ -35,7 +35,7 @@ def gpu_rebuild(sc: scenes.Scene, frames: int | None = None, frame0: int = 0):
     nearest = P.nearest.cpu().numpy().copy()
     for f in range(nf):
         rp = dataclasses.replace(sc.refine, frame_index=frame0 + f,
-                                 accumulate=bool(sc.refine.accumulate and f > 0))
+                                 accumulate=int(sc.refine.accumulate) if f > 0 else 0)
         P.refine(verts, tris, rt.make_refine_params(rp))
     torch.cuda.synchronize()
     out = dict(seed=seed, rep_tri=rep, nearest=nearest,
@@ -54,13 +54,12 @@ def gpu_shadow(grid, sdf: np.ndarray, pos: np.ndarray, nrm: np.ndarray, sp) -> n
 
 
 def compare_rebuild(ref: dict, got: dict, sdf_tol: float = 1e-5, voxels=None):
-    """Bit-exact seeds, rep-tri, flooded seeds; bit-exact refine state and votes at
-    masked voxels; signed field within sdf_tol voxel."""
+    """Bit-exact seeds, rep-tri, flooded seeds; bit-exact refine state and votes (every
+    voxel, or the given sample of masked voxels); signed field within sdf_tol voxel."""
     np.testing.assert_array_equal(got["seed"], ref["seed"])
     np.testing.assert_array_equal(got["rep_tri"], ref["rep_tri"])
     np.testing.assert_array_equal(got["nearest"], ref["nearest"])
-    m = ref["mask"].astype(bool).ravel()
-    sel = np.flatnonzero(m) if voxels is None else np.asarray(voxels)
+    sel = np.arange(ref["mask"].size) if voxels is None else np.asarray(voxels)
     for k in ("dist_bits", "front", "back"):
         np.testing.assert_array_equal(got[k].ravel()[sel], ref[k].ravel()[sel], err_msg=k)
     if voxels is None:

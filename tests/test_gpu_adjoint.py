@@ -45,7 +45,7 @@ def _tracked_rebuild(sc, frames):
         P.build_bvh(verts, tris)
         P.jfa(sc.jfa_steps)
         for f in range(frames):
-            rp = dataclasses.replace(sc.refine, frame_index=f, accumulate=bool(sc.refine.accumulate and f > 0))
+            rp = dataclasses.replace(sc.refine, frame_index=f, accumulate=int(sc.refine.accumulate) if f > 0 else 0)
             P.refine(verts, tris, rt.make_refine_params(rp))
         torch.cuda.synchronize()
         out[track] = dict(dist_bits=P.dist_bits.cpu().numpy().view(np.uint32), front=P.front.cpu().numpy(),
@@ -116,7 +116,7 @@ def _gpu_side(ds, light, s_tgt, v_tgt):
     verts = to_dev(sc.verts).requires_grad_(True)
     L = torch.tensor(light, dtype=torch.float32, requires_grad=True)
     P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), track=True)
-    frames = [dataclasses.replace(sc.refine, frame_index=f, accumulate=bool(sc.refine.accumulate and f > 0))
+    frames = [dataclasses.replace(sc.refine, frame_index=f, accumulate=int(sc.refine.accumulate) if f > 0 else 0)
               for f in range(sc.frames)]
     samples, vis = rt.sdf_shadow(verts, L, P, to_dev(sc.tris), sc.jfa_steps, frames, to_dev(ds.pts),
                                  to_dev(sc.recv_pos), to_dev(sc.recv_nrm), sc.shadow)

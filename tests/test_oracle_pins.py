@@ -515,6 +515,50 @@ def test_refine_converges_with_accumulated_rays(orc):
     assert np.mean(err <= 0.05) >= 0.99
 
 
+def test_decay_accumulation_closed_form(orc):
+    """Eq. (1) (Sec. 2.5.1) without hits is the linear recursion f_t = a f_{t-1} +
+    (1 - a) c, whose solution from f_0 = 0 is (1 - a^t) c; with hits the refined value
+    is the minimum of that blend and the frame's ray distance; a = 0 is a fresh frame
+    and unmasked voxels take c; votes restart every frame."""
+    V, T = scenes.icosphere(2)
+    V = (V * 6.0 + 12.0).astype(np.float32)
+    g = scenes.Grid(24, 24, 24, (0.0, 0.0, 0.0), 1.0)
+    seed, rep, _ = orc.voxelize(V, T, g)
+    near = orc.jfa(g, seed, scenes.jfa_steps(g))
+    u_c, mask = orc.resolve(g, V, T, near, rep, 2.0)
+    m = mask.astype(bool)
+    c = u_c[m].astype(np.float64)
+    alpha = 0.9
+    state = orc.init_refine_state(u_c, mask)
+    zero = np.zeros_like(state[0])
+    state = (zero, state[1] + 3, state[2] + 5) + tuple(state[3:])  # f_0 = 0, stale votes
+    for t in range(1, 13):
+        state = orc.init_refine_state(u_c, mask, state, accumulate=2, alpha=alpha)
+        f = state[0].view(np.float32)
+        np.testing.assert_allclose(f[m], (1 - alpha ** t) * c, rtol=2e-6, atol=1e-6)
+        assert np.all(state[1] == 0) and np.all(state[2] == 0)
+        np.testing.assert_array_equal(f[~m], u_c[~m])
+    fresh = orc.init_refine_state(u_c, mask)
+    a0 = orc.init_refine_state(u_c, mask, state, accumulate=2, alpha=0.0)
+    np.testing.assert_array_equal(a0[0], fresh[0])
+    # with rays: the refined value is min(blend, hits) and never above the blend
+    rp = scenes.RefineParams(rays_per_voxel=16, max_ray_vox=8.0, key=(5, 6), accumulate=2, decay_alpha=alpha)
+    vox = np.flatnonzero(m.ravel()).astype(np.int32)
+    st = orc.init_refine_state(u_c, mask, state, accumulate=2, alpha=alpha)
+    blend = st[0].view(np.float32).ravel().copy()
+    d, fr, bk = (a.ravel().copy() for a in st[:3])
+    orc.refine_voxels(g, V, T, vox, rp, 3, d, fr, bk)
+    fresh_d, ffr, fbk = (a.ravel().copy() for a in fresh[:3])
+    orc.refine_voxels(g, V, T, vox, rp, 3, fresh_d, ffr, fbk)
+    hits = fresh_d.view(np.float32)  # min(c, r_t) of the same rays
+    got = d.view(np.float32)
+    assert np.all(got[vox] <= blend[vox])
+    r_lower = hits[vox] < u_c.ravel()[vox]    # a ray hit below c: then r_t = hits
+    np.testing.assert_array_equal(got[vox][r_lower], np.minimum(blend[vox], hits[vox])[r_lower])
+    np.testing.assert_array_equal(fr, ffr)
+    np.testing.assert_array_equal(bk, fbk)
+
+
 def test_vote_sign_cases(orc):
     p = np.array([0, 0, 1], np.float32)
     a, b, c = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)  # normal +z
