@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extensions", action="store_true", help="skip the backward and batched sections")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the benchmark: stage times over grid size x rays and mask distance x rays")
     return ap.parse_args()
 
 
@@ -578,8 +580,70 @@ def run_ours(args):
     del np
 
 
+def run_sweep(args):
+    """Stage times of the room scene (ms, CUDA events, mean of 5 frames after 2 warm-up
+    frames, fresh refine state each frame) over (a) grid size x rays per voxel and (b)
+    ray-mask distance x rays per voxel at 256x128x256: the axes of the paper's Table 3
+    (size x rays) and Table 4 (mask distance d x rays), on one grid instead of the
+    paper's coarse + fine pair."""
+    import torch
+
+    from paper_2210_06160_gb300 import build
+    from paper_2210_06160_gb300 import rtsdf as rt
+    from paper_2210_06160_gb300 import scenes
+
+    build.build()
+    dev = torch.device("cuda", 0)
+
+    def stages(sc, rays, mask_vox, frames=5, warmup=2):
+        verts = torch.from_numpy(sc.verts).to(dev)
+        tris = torch.from_numpy(sc.tris).to(dev)
+        P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), device=dev)
+        rp = rt.make_refine_params(dataclasses.replace(sc.refine, rays_per_voxel=rays, mask_vox=mask_vox,
+                                                       accumulate=0))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        acc = [0.0] * 4
+        for i in range(warmup + frames):
+            ev[0].record()
+            P.voxelize(verts, tris)
+            ev[1].record()
+            P.build_bvh(verts, tris)
+            ev[2].record()
+            P.jfa(sc.jfa_steps)
+            ev[3].record()
+            P.refine(verts, tris, rp)
+            ev[4].record()
+            torch.cuda.synchronize()
+            if i >= warmup:
+                for j in range(4):
+                    acc[j] += ev[j].elapsed_time(ev[j + 1]) / frames
+        c = rt.counters_dict(P.counters)
+        del P
+        torch.cuda.empty_cache()
+        return {"voxelize": round(acc[0], 3), "bvh": round(acc[1], 3), "jfa": round(acc[2], 3),
+                "refine": round(acc[3], 3), "masked_voxels": c["masked_voxels"] // (warmup + frames)}
+
+    size_rays = []
+    for nx in (128, 256, 512):
+        sc = scenes.scene_room(nx=nx, ny=nx // 2, nz=nx, shadow_w=64, shadow_h=36)
+        for rays in (1, 5, 10):
+            size_rays.append({"grid": [nx, nx // 2, nx], "rays": rays, **stages(sc, rays, 4.0)})
+    sc = scenes.scene_room(nx=256, ny=128, nz=256, shadow_w=64, shadow_h=36)
+    h = sc.grid.h
+    mask_rays = []
+    for d in (0.01, 0.05, 0.1, 0.5, None):
+        mv = 1e6 if d is None else d / h
+        for rays in (1, 5, 10, 15):
+            mask_rays.append({"d_world": d, "mask_vox": round(mv, 3) if d is not None else "all", "rays": rays,
+                              **stages(sc, rays, mv)})
+    print(json.dumps({"sweep": "room scene", "size_x_rays": size_rays, "mask_x_rays_256x128x256": mask_rays}))
+
+
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

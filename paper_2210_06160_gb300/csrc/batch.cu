@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(512) k_bresolve(const __grid_constant__ BatchT
                              (int32_t)(si << kBrickBits), smask);
 }
 
-template <int BX, int BY, int BZ>
+template <int BX, int BY, int BZ, int RPL>
 __global__ void __launch_bounds__(kRefineMaxThreads, kRefineWarpsPerSm * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t, BatchGrids G,
                                                                   uint32_t frame, int accumulate,
                                                                   const char* __restrict__ bvh,
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kRefineMaxThreads, kRefineWarpsPerSm * 32 / kR
         const int n_inner = n_leaves > 1 ? n_leaves - 1 : 1;
         const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
         const int64_t o = S.vox_off;
-        refine_brick<BX, BY, BZ, false>(a, nodes, leaves, n_leaves, n_inner, (S.flood_b ? G.buf_b : G.buf_a) + o,
+        refine_brick<BX, BY, BZ, false, RPL>(a, nodes, leaves, n_leaves, n_inner, (S.flood_b ? G.buf_b : G.buf_a) + o,
                                         G.rep_tri + o, bmask[S.brick_off + b], bx, by, bz, G.dist_bits + o,
                                         G.front + o, G.back + o, G.sdf + o, nullptr, nullptr, w, n_hit, n_fail,
                                         n_ovf);
@@ -515,7 +515,7 @@ rtsdf_status run_jfa(rtsdf_batch_plan& P, uint32_t* a, uint32_t* b, cudaStream_t
     return RTSDF_OK;
 }
 
-template <int BX, int BY, int BZ>
+template <int BX, int BY, int BZ, int RPL>
 rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers& B, uint32_t frame, int accumulate,
                            rtsdf_counters* counters, int warps, cudaStream_t s) {
     const Shape sh{BX, BY, BZ};
@@ -533,12 +533,12 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(sizeof(WarpSmem) * 4)));
         attr_set[dev] = true;
     }
     // the same resident warps per SM for every CTA size (shared memory bound)
-    k_brefine<BX, BY, BZ><<<num_sms() * (kRefineWarpsPerSm / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
+    k_brefine<BX, BY, BZ, RPL><<<num_sms() * (kRefineWarpsPerSm / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
                                                                             static_cast<const char*>(B.bvh), bmask,
                                                                             blist, count, counters);
     RTSDF_LAUNCHED();
@@ -554,9 +554,16 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
 rtsdf_status refine_step(const rtsdf_batch_plan& P, const rtsdf_batch_buffers& B, uint32_t frame, int accumulate,
                          rtsdf_counters* counters, const rtsdf_batch_tuning& tu, cudaStream_t s) {
     const int w = tu.warps_per_cta;
-    if (tu.brick_x == 4) return launch_refine<4, 4, 4>(P, B, frame, accumulate, counters, w, s);
-    if (tu.brick_x == 8) return launch_refine<8, 4, 2>(P, B, frame, accumulate, counters, w, s);
-    return launch_refine<16, 2, 2>(P, B, frame, accumulate, counters, w, s);
+    int rmax = 1;  // one ray group per brick for up to rpl rays (the largest ray count of the batch)
+    for (const rtsdf_batch_scene& sc : P.scenes) rmax = sc.refine.rays_per_voxel > rmax ? sc.refine.rays_per_voxel : rmax;
+    const int rpl = rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8);
+#define RTSDF_BATCH_CASE(X, Y, Z, R) \
+    if (tu.brick_x == X && rpl == R) return launch_refine<X, Y, Z, R>(P, B, frame, accumulate, counters, w, s);
+    RTSDF_BATCH_CASE(4, 4, 4, 2) RTSDF_BATCH_CASE(4, 4, 4, 4) RTSDF_BATCH_CASE(4, 4, 4, 8)
+    RTSDF_BATCH_CASE(8, 4, 2, 2) RTSDF_BATCH_CASE(8, 4, 2, 4) RTSDF_BATCH_CASE(8, 4, 2, 8)
+    RTSDF_BATCH_CASE(16, 2, 2, 2) RTSDF_BATCH_CASE(16, 2, 2, 4) RTSDF_BATCH_CASE(16, 2, 2, 8)
+#undef RTSDF_BATCH_CASE
+    return RTSDF_EINVAL;
 }
 
 rtsdf_status buffers_ok(const rtsdf_batch_plan* P, const rtsdf_batch_buffers* b) {

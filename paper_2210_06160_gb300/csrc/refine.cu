@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __
 // ------------------------------------------------------------------ refine
 
 // Persistent: warps take bricks from the work list until it is exhausted.
-template <bool kTrack>
+template <bool kTrack, int RPL>
 __global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefineThreads) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefi
         if (wk >= nact) break;
         const int b = blist[wk];
         const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
-        refine_brick<kBX, kBY, kBZ, kTrack>(a, nodes, leaves, n_leaves, n_inner, nearest, rep_tri, bmask[b], bx, by,
+        refine_brick<kBX, kBY, kBZ, kTrack, RPL>(a, nodes, leaves, n_leaves, n_inner, nearest, rep_tri, bmask[b], bx, by,
                                             bz, dist_bits, front, back, sdf, win_ray, win_tri, w, n_hit, n_fail,
                                             n_ovf);
     }
@@ -111,6 +111,42 @@ __global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefi
         if (n_fail) atomicAdd(&counters->rays_failed, n_fail);
     }
     if (lane == 0 && n_ovf) atomicAdd(count + 2, n_ovf);
+}
+
+template <bool kTrack, int RPL>
+static rtsdf_status launch_refine_t(size_t smem, cudaStream_t s, const RefineArgs& a, const BvhHeader* hdr,
+                                    const BvhNode* nodes, const BvhLeaf* leaves, const int32_t* nearest,
+                                    const int32_t* rep_tri, const unsigned long long* bmask, const int32_t* blist,
+                                    uint32_t* count, uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
+                                    rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    RTSDF_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        RTSDF_CUDA(cudaFuncSetAttribute(k_refine<kTrack, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[dev] = true;
+    }
+    k_refine<kTrack, RPL><<<num_sms() * (kRefineWarpsPerSm * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
+        a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count, dist_bits, front, back, sdf, counters, win_ray,
+        win_tri);
+    return RTSDF_OK;
+}
+
+static rtsdf_status launch_refine_kernel(bool track, int rpl, size_t smem, cudaStream_t s, const RefineArgs& a,
+                                         const BvhHeader* hdr, const BvhNode* nodes, const BvhLeaf* leaves,
+                                         const int32_t* nearest, const int32_t* rep_tri,
+                                         const unsigned long long* bmask, const int32_t* blist, uint32_t* count,
+                                         uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
+                                         rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
+#define RTSDF_REFINE_CASE(T, R)                                                                                 \
+    if (track == T && rpl == R)                                                                                 \
+        return launch_refine_t<T, R>(smem, s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count,     \
+                                     dist_bits, front, back, sdf, counters, T ? win_ray : nullptr,              \
+                                     T ? win_tri : nullptr);
+    RTSDF_REFINE_CASE(false, 2) RTSDF_REFINE_CASE(false, 4) RTSDF_REFINE_CASE(false, 8)
+    RTSDF_REFINE_CASE(true, 2) RTSDF_REFINE_CASE(true, 4) RTSDF_REFINE_CASE(true, 8)
+#undef RTSDF_REFINE_CASE
+    return RTSDF_EINVAL;
 }
 
 // Masked voxels (set bits over all bricks) and walks that overflowed, to the counters.
@@ -162,22 +198,9 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
                                     track ? win_ray : nullptr, track ? win_tri : nullptr);
     RTSDF_LAUNCHED();
     const size_t smem = sizeof(WarpSmem) * (kRefineThreads / 32);
-    static bool attr_set[64][2] = {};
-    int dev = 0;
-    RTSDF_CUDA(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && !attr_set[dev][track]) {
-        RTSDF_CUDA(cudaFuncSetAttribute(track ? k_refine<true> : k_refine<false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set[dev][track] = true;
-    }
-    if (track)
-        k_refine<true><<<num_sms() * (kRefineWarpsPerSm * 32 / kRefineThreads), kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
-                                                                 w.blist, w.count, dist_bits, front, back, sdf,
-                                                                 counters, win_ray, win_tri);
-    else
-        k_refine<false><<<num_sms() * (kRefineWarpsPerSm * 32 / kRefineThreads), kRefineThreads, smem, s>>>(a, hdr, nodes, leaves, nearest, rep_tri, w.bmask,
-                                                                  w.blist, w.count, dist_bits, front, back, sdf,
-                                                                  counters, nullptr, nullptr);
+    const int rpl = a.R <= 2 ? 2 : (a.R <= 4 ? 4 : 8);  // one ray group for up to rpl rays
+    RTSDF_TRY(launch_refine_kernel(track, rpl, smem, s, a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
+                                   w.count, dist_bits, front, back, sdf, counters, win_ray, win_tri));
     RTSDF_LAUNCHED();
     if (counters) {
         k_refine_report<<<num_sms(), 256, 0, s>>>(w.count, w.bmask, nbricks(gh), counters);

@@ -14,7 +14,7 @@ namespace rtsdf {
 constexpr int kListCap = 256;        // staged leaves per warp and round
 constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
 constexpr int kNarrowMargin = 96;    // > depth of any tree the builder makes (30-bit codes + 32 index bits)
-constexpr int kRaysPerLane = 8;      // rays of a voxel per group (one lane per voxel)
+constexpr int kRaysPerLane = 8;      // most rays of a voxel per group (one lane per voxel)
 constexpr int kFilterBatch = 2;      // staged triangles filtered per enqueue
 constexpr int kQueueCap = 32 + 32 * 8 * kFilterBatch;  // queued ray/triangle items per warp
 constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
@@ -260,6 +260,7 @@ __device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict_
 // division as |sd - h dn| <= h |dn| (h = tmax / 2) and widened by eps in sd.  All
 // margins exceed the FP32 rounding of both sides, so no triangle the exact test
 // accepts is dropped.
+template <int RPL>
 __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf, float3 o, uint32_t okm,
                                                 const float2* dx2, const float2* dy2, const float2* dz2,
                                                 float tmax) {
@@ -283,7 +284,7 @@ __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf
     const float2 sd2 = make_float2(sd, sd), mh2 = make_float2(-h, -h);
     uint32_t pm = 0;
 #pragma unroll
-    for (int r = 0; r < kRaysPerLane / 2; ++r) {
+    for (int r = 0; r < RPL / 2; ++r) {
         const float2 tc = __ffma2_rn(cx2, dx2[r], __ffma2_rn(cy2, dy2[r], __fmul2_rn(cz2, dz2[r])));
         const float2 dn = __ffma2_rn(nx2, dx2[r], __ffma2_rn(ny2, dy2[r], __fmul2_rn(nz2, dz2[r])));
         const float2 u = __ffma2_rn(mh2, dn, sd2);  // sd - h dn
@@ -305,7 +306,9 @@ __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf
 // not diverge.  Both filters are conservative (their margins exceed FP32 rounding
 // of the exact test), so they never drop a triangle the exact test accepts; they
 // may use fused multiply-adds because they decide nothing the oracle decides.
-template <int BX, int BY, int BZ, bool kTrack>
+// RPL: rays per lane and group (2, 4 or 8); calls with R <= RPL rays per voxel run
+// one group, so small ray counts do not pay for eight.
+template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane>
 __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode* __restrict__ nodes,
                                              const BvhLeaf* __restrict__ leaves, int n_leaves, int n_inner,
                                              const int32_t* __restrict__ nearest,
@@ -359,11 +362,11 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
         // tracked: this call's winning ray, ordered by (t, triangle id), first ray on ties
         unsigned long long wkey = ~0ull;
         uint32_t wray = 0xFFFFFFFFu;
-        for (int r0 = 0; r0 < a.R; r0 += kRaysPerLane) {
-            float3 dir[kRaysPerLane];
+        for (int r0 = 0; r0 < a.R; r0 += RPL) {
+            float3 dir[RPL];
             uint32_t okm = 0;
 #pragma unroll
-            for (int r = 0; r < kRaysPerLane; ++r) {
+            for (int r = 0; r < RPL; ++r) {
                 const int ray = r0 + r;
                 dir[r] = make_float3(0.f, 0.f, 1.f);
                 if (mine && ray < a.R) {
@@ -378,9 +381,9 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                 w.dirz[r][lane] = dir[r].z;
                 w.key[r][lane] = ~0ull;
             }
-            float2 dx2[kRaysPerLane / 2], dy2[kRaysPerLane / 2], dz2[kRaysPerLane / 2];
+            float2 dx2[RPL / 2], dy2[RPL / 2], dz2[RPL / 2];
 #pragma unroll
-            for (int r = 0; r < kRaysPerLane / 2; ++r) {
+            for (int r = 0; r < RPL / 2; ++r) {
                 dx2[r] = make_float2(dir[2 * r].x, dir[2 * r + 1].x);
                 dy2[r] = make_float2(dir[2 * r].y, dir[2 * r + 1].y);
                 dz2[r] = make_float2(dir[2 * r].z, dir[2 * r + 1].z);
@@ -406,7 +409,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
 #pragma unroll
                     for (int j = 0; j < kFilterBatch; ++j) {
                         const int c = c0 + j;
-                        if (c < nc) pm4 |= filter_rays(leaves + w.list[c], o, okm, dx2, dy2, dz2, a.tmax) << (8 * j);
+                        if (c < nc) pm4 |= filter_rays<RPL>(leaves + w.list[c], o, okm, dx2, dy2, dz2, a.tmax) << (8 * j);
                     }
                     if (pm4) {
                         int pos = atomicAdd(&w.qn, __popc(pm4));
@@ -439,7 +442,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             }
             // closest hits of this lane's rays
 #pragma unroll
-            for (int r = 0; r < kRaysPerLane; ++r) {
+            for (int r = 0; r < RPL; ++r) {
                 const unsigned long long key = w.key[r][lane];
                 if (key != ~0ull) {
                     vbest = min(vbest, (uint32_t)(key >> 32));
