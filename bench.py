@@ -238,6 +238,63 @@ def bench_dynamic(dev, frames: int = 120, warmup: int = 3) -> dict:
     return out
 
 
+def bench_two_res(dev, steps: int = 10, warmup: int = 3) -> dict:
+    """Sec. 2.5.1 two resolutions on the room: seeds and jump flooding on a 200x100x200
+    coarse grid, coarse field, mask (2 coarse voxels = 4 fine) and refinement (8 rays,
+    accumulated) on the 400x200x400 fine grid, then the 1920x1080 shadow."""
+    import torch
+
+    from paper_2210_06160_gb300 import rtsdf as rt
+    from paper_2210_06160_gb300 import scenes
+
+    sc = scenes.scene_room()
+    gf = sc.grid
+    gc = scenes.Grid(gf.nx // 2, gf.ny // 2, gf.nz // 2, gf.origin, gf.h * 2)
+    steps_c = scenes.jfa_steps(gc, extra_one=True)
+    verts = torch.from_numpy(sc.verts).to(dev)
+    tris = torch.from_numpy(sc.tris).to(dev)
+    pos = torch.from_numpy(sc.recv_pos).to(dev)
+    nrm = torch.from_numpy(sc.recv_nrm).to(dev)
+    P = rt.TwoResPipeline(gf, gc, len(sc.verts), len(sc.tris), device=dev)
+    sp = rt.make_shadow_params(sc.shadow)
+    vis = torch.empty(len(sc.recv_pos), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def frame(f, ev=None):
+        rp = rt.make_refine_params(dataclasses.replace(sc.refine, mask_vox=2.0, frame_index=f, accumulate=f > 0))
+        if ev:
+            ev[0].record(stream)
+        P.coarse.voxelize(verts, tris)
+        P.fine.build_bvh(verts, tris)
+        near = P.coarse.jfa(steps_c)
+        if ev:
+            ev[1].record(stream)
+        f_ = P.fine
+        rt.rtsdf_refine_2res(P.gf, P.gc, verts, tris, f_.bvh, near, P.coarse.rep_tri, rp, f_.dist_bits, f_.front,
+                             f_.back, f_.sdf, f_.ws_refine, f_.counters)
+        if ev:
+            ev[2].record(stream)
+        P.shadow(pos, nrm, sp, vis)
+        if ev:
+            ev[3].record(stream)
+
+    for f in range(warmup):
+        frame(f)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(steps):
+        frame(warmup + i, evs[i])
+    torch.cuda.synchronize()
+    mean = lambda a, b: statistics.mean(e[a].elapsed_time(e[b]) for e in evs)
+    out = {"workload": "room, coarse 200x100x200 (voxelize + JFA), fine 400x200x400 (BVH, resolve, refine 8 rays, "
+                       "field), 1920x1080 shadow",
+           "frame_ms": round(mean(0, 3), 4), "voxelize_bvh_jfa_ms": round(mean(0, 1), 4),
+           "refine_ms": round(mean(1, 2), 4), "shadow_ms": round(mean(2, 3), 4), "steps": steps}
+    del P
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batch(dev, steps: int = 5, warmup: int = 2) -> dict:
     """48 seeded scenes of uneven sizes (dims from 32^3 .. 256x128x256, 500-60k
     triangles, 8 rays/voxel): one batched rebuild (voxelize + BVH + JFA + refine,
@@ -553,11 +610,12 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h_verts.numel() * 4 + h_tris.numel() * 4),
                "d2h_bytes_per_step": int(h_sdf.numel() * 4 + h_vis.numel() * 4), "steps": ke}
 
-    bwd = batch = dyn = None
+    bwd = batch = dyn = two = None
     if args.workload == "room" and not args.no_extensions:
         bwd = bench_backward(dev)
         batch = bench_batch(dev)
         dyn = bench_dynamic(dev)
+        two = bench_two_res(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -572,7 +630,7 @@ def run_ours(args):
                 "rebuild_ms": round(rebuild_ms, 4),
                 "stage_ms": {k: round(v, 4) for k, v in stage.items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "backward": bwd, "batch": batch, "dynamic": dyn,
+                "backward": bwd, "batch": batch, "dynamic": dyn, "two_resolution": two,
                 "clocks": clk, "counters": counters, "impl": "ours"}
         print(json.dumps(line), flush=True)
     if world > 1:

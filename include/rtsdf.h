@@ -215,6 +215,22 @@ rtsdf_status rtsdf_refine_tracked(const rtsdf_grid* g, const float* verts, int32
                                   int32_t* win_tri, void* ws, size_t ws_bytes, rtsdf_counters* counters,
                                   rtsdf_stream stream);
 
+/* Two resolutions (Sec. 2.5.1: JFA on a coarse grid, e.g. 128^3, the refined field on
+ * a fine grid, e.g. 256^3).  Same as rtsdf_refine on the FINE grid `fine` (state,
+ * sdf_out and workspace are fine grids; the BVH is built for the fine grid), except
+ * that `nearest` (flooded seeds) and `rep_tri` are grids of `coarse`: fine voxel
+ * (i,j,k) takes the seed of coarse voxel (i/r, j/r, k/r), r = coarse h / fine h (a
+ * positive integer, same origin, coarse dims = ceil(fine dims / r), else
+ * RTSDF_EINVAL); u_c is the distance from the fine voxel's centre to that seed's
+ * representative triangle; the mask compares the integer seed distance in COARSE
+ * voxels with mask_vox^2 (mask_vox in coarse voxels).  beta_vox and max_ray_vox are
+ * in fine voxels.  rtsdf_backward supports single-resolution fields only. */
+rtsdf_status rtsdf_refine_2res(const rtsdf_grid* fine, const rtsdf_grid* coarse, const float* verts, int32_t V,
+                               const int32_t* tris, int32_t T, const void* bvh, size_t bvh_bytes,
+                               const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params* p,
+                               uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf_out, void* ws,
+                               size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream);
+
 /* ---------------------------------------------------------------- shadow */
 
 /* Sec. 2.4 sphere tracing toward a directional light with the penumbra estimate

@@ -67,6 +67,8 @@ def lib():
                 "or_vote_sign": (C.c_int, [u32, u32, P, P, P, P, C.c_int]),
                 "or_finalize": (None, [G, P, P, P, P, P, P, P, P, P, f32, C.c_int, P]),
                 "or_trilinear": (f32, [G, P, f32, f32, f32]),
+                "or_resolve_2res": (None, [G, G, i32, P, P, P, P, f32, f32, P, P]),
+                "or_fine_rep_2res": (None, [G, G, i32, P, P, P]),
                 "or_sample": (None, [G, P, P, i32, P]),
                 "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P]),
                 "or_num_threads": (C.c_int, []),
@@ -221,6 +223,45 @@ def finalize(grid, vv, tris, nearest, rep_tri, mask, u_c, dist_bits, front, back
     lib().or_finalize(C.byref(_g(grid)), *[_p(a) for a in arrs], float(rp.beta_vox),
                       int(bool(rp.sign_fallback)), _p(sdf))
     return sdf
+
+
+def resolve_2res(grid_f, grid_c, ratio, vv_f, tris, nearest_c, rep_c, mask_vox):
+    """Sec. 2.5.1 two resolutions: (u_c, mask) on the fine grid from the coarse seeds."""
+    u_c = np.empty(grid_f.shape_zyx, dtype=np.float32)
+    mask = np.empty(grid_f.shape_zyx, dtype=np.uint8)
+    lib().or_resolve_2res(C.byref(_g(grid_f)), C.byref(_g(grid_c)), int(ratio), _p(_f32(vv_f)), _p(_i32(tris)),
+                          _p(_i32(nearest_c)), _p(_i32(rep_c)), float(mask_vox),
+                          float(grid_f.nx + grid_f.ny + grid_f.nz), _p(u_c), _p(mask))
+    return u_c, mask
+
+
+def rebuild_2res(scene, grid_c, steps_c, frames: int = 1, frame0: int = 0, voxel_subset=None):
+    """Two-resolution rebuild (Sec. 2.5.1): voxelize and flood on the coarse grid
+    grid_c, resolve and refine on the scene's (fine) grid; scene.refine.mask_vox is in
+    coarse voxels."""
+    gf, rp = scene.grid, scene.refine
+    ratio = int(round(grid_c.h / gf.h))
+    vv_c = to_voxel(scene.verts, grid_c)
+    seed_c, rep_c, _ = voxelize(vv_c, scene.tris, grid_c)
+    near_c = jfa(grid_c, seed_c, steps_c)
+    vv = to_voxel(scene.verts, gf)
+    u_c, mask = resolve_2res(gf, grid_c, ratio, vv, scene.tris, near_c, rep_c, rp.mask_vox)
+    masked = np.flatnonzero(mask.ravel()).astype(np.int32)
+    todo = masked if voxel_subset is None else np.intersect1d(masked, voxel_subset).astype(np.int32)
+    state = None
+    for f in range(frames):
+        state = init_refine_state(u_c, mask, state, accumulate=rp.accumulate, alpha=rp.decay_alpha)
+        d, fr, bk = (a.ravel().copy() for a in state[:3])
+        refine_voxels(gf, vv, scene.tris, todo, rp, frame0 + f, d, fr, bk)
+        state = (d.reshape(gf.shape_zyx), fr.reshape(gf.shape_zyx), bk.reshape(gf.shape_zyx)) + tuple(state[3:])
+    rep_f = np.empty(gf.shape_zyx, dtype=np.int32)
+    lib().or_fine_rep_2res(C.byref(_g(gf)), C.byref(_g(grid_c)), ratio, _p(_i32(near_c)), _p(_i32(rep_c)),
+                           _p(rep_f))
+    k, j, i = np.meshgrid(np.arange(gf.nz), np.arange(gf.ny), np.arange(gf.nx), indexing="ij")
+    self_seed = ((k << 20) | (j << 10) | i).astype(np.int32)   # each voxel its own seed: rep_f per voxel
+    sdf = finalize(gf, vv, scene.tris, self_seed, rep_f, mask, u_c, *state[:3], rp)
+    return dict(seed_c=seed_c, rep_c=rep_c, nearest_c=near_c, u_c=u_c, mask=mask, masked=masked,
+                dist_bits=state[0], front=state[1], back=state[2], sdf=sdf)
 
 
 def shadow(grid, sdf, pos, nrm, sp) -> np.ndarray:

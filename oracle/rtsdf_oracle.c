@@ -307,6 +307,55 @@ void or_resolve(const or_grid* g, const float* vv, const int32_t* tris, const in
             }
 }
 
+/* Two resolutions (Sec. 2.5.1: the coarse SDF by jump flooding at 128^3, the fine
+ * SDF at 256^3): fine voxel (i,j,k) lies in coarse voxel (i/r, j/r, k/r); its
+ * flooded seed and representative triangle are that coarse voxel's; the distance
+ * is measured from the fine voxel's centre (vv in fine voxel units); the mask
+ * compares the integer seed distance in coarse voxels. */
+void or_resolve_2res(const or_grid* gf, const or_grid* gc, int32_t ratio, const float* vv, const int32_t* tris,
+                     const int32_t* nearest_c, const int32_t* rep_c, float mask_vox, float empty_dist, float* u_c,
+                     uint8_t* mask) {
+    const int nx = gf->nx, ny = gf->ny, nz = gf->nz;
+    const float m2 = mask_vox * mask_vox;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int64_t lin = ((int64_t)k * ny + j) * nx + i;
+                const int ic = i / ratio, jc = j / ratio, kc = k / ratio;
+                const int32_t s = nearest_c[((int64_t)kc * gc->ny + jc) * gc->nx + ic];
+                int32_t rep = -1;
+                if (s != OR_EMPTY)
+                    rep = rep_c[((int64_t)((s >> 20) & 1023) * gc->ny + ((s >> 10) & 1023)) * gc->nx + (s & 1023)];
+                if (rep < 0) {
+                    u_c[lin] = empty_dist;
+                    mask[lin] = 0;
+                    continue;
+                }
+                const float p[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};
+                const int32_t* tr = tris + 3 * (int64_t)rep;
+                u_c[lin] = sqrtf(or_closest_d2(p, vv + 3 * (int64_t)tr[0], vv + 3 * (int64_t)tr[1],
+                                               vv + 3 * (int64_t)tr[2]));
+                mask[lin] = ((float)seed_d2(ic, jc, kc, s) <= m2) ? 1 : 0;
+            }
+}
+
+/* The representative triangle each fine voxel's sign fallback uses (that of its
+ * coarse voxel's flooded seed), as a fine grid. */
+void or_fine_rep_2res(const or_grid* gf, const or_grid* gc, int32_t ratio, const int32_t* nearest_c,
+                      const int32_t* rep_c, int32_t* rep_f) {
+    const int nx = gf->nx, ny = gf->ny, nz = gf->nz;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int32_t s = nearest_c[((int64_t)(k / ratio) * gc->ny + j / ratio) * gc->nx + i / ratio];
+                rep_f[((int64_t)k * ny + j) * nx + i] =
+                    s == OR_EMPTY ? -1
+                                  : rep_c[((int64_t)((s >> 20) & 1023) * gc->ny + ((s >> 10) & 1023)) * gc->nx +
+                                          (s & 1023)];
+            }
+}
+
 /* ------------------------------------------------------------------ Philox */
 
 /* Philox4x32 with 10 rounds: each round multiplies words 0 and 2 by the two

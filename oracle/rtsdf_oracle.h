@@ -61,6 +61,15 @@ void or_resolve(const or_grid* g, const float* vv, const int32_t* tris, const in
                 const int32_t* rep_tri, float mask_vox, float empty_dist,
                 float* u_c, uint8_t* mask);
 
+/* Two resolutions (Sec. 2.5.1): resolve fine voxels against the flooded seeds and
+ * representative triangles of the coarse grid gc (ratio = fine voxels per coarse
+ * voxel); the mask is on the integer seed distance in coarse voxels. */
+void or_resolve_2res(const or_grid* gf, const or_grid* gc, int32_t ratio, const float* vv, const int32_t* tris,
+                     const int32_t* nearest_c, const int32_t* rep_c, float mask_vox, float empty_dist, float* u_c,
+                     uint8_t* mask);
+void or_fine_rep_2res(const or_grid* gf, const or_grid* gc, int32_t ratio, const int32_t* nearest_c,
+                      const int32_t* rep_c, int32_t* rep_f);
+
 /* Philox4x32-10 (Salmon et al., SC'11). */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 

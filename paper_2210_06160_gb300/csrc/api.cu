@@ -95,11 +95,32 @@ size_t rtsdf_refine_workspace(const rtsdf_grid* g) { return grid_ok(g) ? refine_
 
 namespace {
 
+// The coarse grid of a two-resolution call: same origin, an edge of `ratio` fine
+// edges (ratio a positive integer, to 1e-6 relative), dims = ceil(fine dims / ratio).
+int coarse_ratio(const rtsdf_grid* fine, const rtsdf_grid* coarse) {
+    if (!grid_ok(coarse)) return 0;
+    for (int a = 0; a < 3; ++a)
+        if (coarse->origin[a] != fine->origin[a]) return 0;
+    const double r = (double)coarse->h / (double)fine->h;
+    const int ri = (int)(r + 0.5);
+    if (ri < 1 || ri > 64 || fabs(r - ri) > 1e-6 * r) return 0;
+    if (coarse->nx != (fine->nx + ri - 1) / ri || coarse->ny != (fine->ny + ri - 1) / ri ||
+        coarse->nz != (fine->nz + ri - 1) / ri)
+        return 0;
+    return ri;
+}
+
 rtsdf_status refine_checked(const rtsdf_grid* g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
                             const void* bvh, size_t bvh_bytes_, const int32_t* nearest, const int32_t* rep_tri,
                             const rtsdf_refine_params* p, uint32_t* dist_bits, uint32_t* front, uint32_t* back,
                             float* sdf_out, uint32_t* win_ray, int32_t* win_tri, void* ws, size_t ws_bytes,
-                            rtsdf_counters* counters, rtsdf_stream stream) {
+                            rtsdf_counters* counters, rtsdf_stream stream, const rtsdf_grid* coarse = nullptr) {
+    int ratio = 1;
+    if (coarse) {
+        if (!grid_ok(g)) return RTSDF_EINVAL;
+        ratio = coarse_ratio(g, coarse);
+        if (ratio == 0) return RTSDF_EINVAL;
+    }
     if (!grid_ok(g) || !mesh_ok(verts, V, tris, T) || !p) return RTSDF_EINVAL;
     if (!buf_ok(bvh, 256) || !buf_ok(nearest, 16) || !buf_ok(rep_tri, 16) || !buf_ok(dist_bits, 16) ||
         !buf_ok(front, 16) || !buf_ok(back, 16) || !buf_ok(sdf_out, 16) || !buf_ok(ws, 256))
@@ -113,7 +134,7 @@ rtsdf_status refine_checked(const rtsdf_grid* g, const float* verts, int32_t V, 
     if (bvh_bytes_ < bvh_bytes(T)) return RTSDF_ENOMEM;
     if (ws_bytes < refine_workspace(*g)) return RTSDF_ENOMEM;
     return refine(*g, verts, V, tris, T, bvh, nearest, rep_tri, *p, dist_bits, front, back, sdf_out, ws, counters,
-                  win_ray, win_tri, cs(stream));
+                  win_ray, win_tri, coarse, ratio, cs(stream));
 }
 
 bool refine_params_ok(const rtsdf_refine_params* p) {
@@ -146,6 +167,16 @@ rtsdf_status rtsdf_refine_tracked(const rtsdf_grid* g, const float* verts, int32
     if (!buf_ok(win_ray, 16) || !buf_ok(win_tri, 16)) return RTSDF_EINVAL;
     return refine_checked(g, verts, V, tris, T, bvh, bvh_bytes_, nearest, rep_tri, p, dist_bits, front, back, sdf_out,
                           win_ray, win_tri, ws, ws_bytes, counters, stream);
+}
+
+rtsdf_status rtsdf_refine_2res(const rtsdf_grid* fine, const rtsdf_grid* coarse, const float* verts, int32_t V,
+                               const int32_t* tris, int32_t T, const void* bvh, size_t bvh_bytes_,
+                               const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params* p,
+                               uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf_out, void* ws,
+                               size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream) {
+    if (!coarse) return RTSDF_EINVAL;
+    return refine_checked(fine, verts, V, tris, T, bvh, bvh_bytes_, nearest, rep_tri, p, dist_bits, front, back,
+                          sdf_out, nullptr, nullptr, ws, ws_bytes, counters, stream, coarse);
 }
 
 rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm, int32_t P,

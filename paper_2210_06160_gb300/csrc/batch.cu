@@ -251,6 +251,10 @@ __device__ __forceinline__ RefineArgs scene_args(const SceneD& S, const float* v
     a.fallback = S.fallback;
     a.alpha = S.alpha;
     a.one_minus_alpha = 1.0f - S.alpha;
+    a.ratio = 1;
+    a.cnx = S.g.nx;
+    a.cny = S.g.ny;
+    a.cnz = S.g.nz;
     a.nbx = (S.g.nx + BX - 1) / BX;
     a.nby = (S.g.ny + BY - 1) / BY;
     a.nbz = (S.g.nz + BZ - 1) / BZ;

@@ -163,7 +163,8 @@ __global__ void k_refine_report(const uint32_t* __restrict__ count, const unsign
 rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const int32_t* tris, int32_t T,
                     const void* bvh, const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params& p,
                     uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf, void* ws,
-                    rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, cudaStream_t s) {
+                    rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, const rtsdf_grid* coarse,
+                    int ratio, cudaStream_t s) {
     RefineArgs a;
     a.g = to_dev(gh);
     a.verts = verts;
@@ -183,6 +184,10 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
     a.alpha = p.decay_alpha;
     a.one_minus_alpha = 1.0f - p.decay_alpha;
     a.fallback = p.sign_fallback;
+    a.ratio = coarse ? ratio : 1;
+    a.cnx = coarse ? coarse->nx : gh.nx;
+    a.cny = coarse ? coarse->ny : gh.ny;
+    a.cnz = coarse ? coarse->nz : gh.nz;
     a.nbx = (gh.nx + kBX - 1) / kBX;
     a.nby = (gh.ny + kBY - 1) / kBY;
     a.nbz = (gh.nz + kBZ - 1) / kBZ;

@@ -42,12 +42,25 @@ struct RefineArgs {
     int accumulate, fallback;
     float alpha, one_minus_alpha;  // Eq. (1) decay (accumulate = 2)
     int nbx, nby, nbz;  // brick grid
+    int ratio;          // fine voxels per coarse voxel along each axis (1: one grid)
+    int cnx, cny, cnz;  // coarse grid of the flooded seeds and representative triangles
 };
 
 constexpr int kMaxBricksPerTile = 16;
 
+// Index of the coarse voxel holding fine voxel (i, j, k) (the two-resolution form of
+// Sec. 2.5.1: flooded seeds and representative triangles live on the coarse grid).
+__device__ __forceinline__ int64_t coarse_index(const RefineArgs& a, int i, int j, int k, int& ic, int& jc, int& kc) {
+    ic = a.ratio == 1 ? i : i / a.ratio;
+    jc = a.ratio == 1 ? j : j / a.ratio;
+    kc = a.ratio == 1 ? k : k / a.ratio;
+    return ((int64_t)kc * a.cny + jc) * a.cnx + ic;
+}
+
 // One 32x4x4 tile of voxels (512 threads, tile coordinates tb): coarse distance u_c
-// to the representative triangle of the flooded seed; unmasked voxels get their
+// to the representative triangle of the flooded seed (with two resolutions: the
+// seed of the coarse voxel holding the fine voxel; the mask compares the integer
+// seed distance in coarse voxels); unmasked voxels get their
 // final value (u_c - beta) and the state (u_c, 0, 0); masked voxels initialise their
 // refine state (and, when tracked, the coarse source takes the winner record where
 // it sets the distance).
@@ -69,21 +82,22 @@ __device__ __forceinline__ void resolve_tile(const RefineArgs& a, int3 tb, const
     bool masked = false;
     if (i < a.g.nx && j < a.g.ny && k < a.g.nz) {
         const int64_t lin = ((int64_t)k * a.g.ny + j) * a.g.nx + i;
-        const int32_t s = __ldg(nearest + lin);
+        int ic, jc, kc;
+        const int32_t s = __ldg(nearest + coarse_index(a, i, j, k, ic, jc, kc));
         int32_t rep = -1;
         int si = 0, sj = 0, sk = 0;
         if (s != RTSDF_EMPTY) {
             si = s & 1023;
             sj = (s >> 10) & 1023;
             sk = (s >> 20) & 1023;
-            rep = __ldg(rep_tri + ((int64_t)sk * a.g.ny + sj) * a.g.nx + si);
+            rep = __ldg(rep_tri + ((int64_t)sk * a.cny + sj) * a.cnx + si);
         }
         float uc = a.empty_dist;
         float3 A, B, C;
         if (rep >= 0 && load_tri(a.verts, a.V, a.tris, rep, a.g, A, B, C)) {
             const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
             uc = sqrtf(closest_d2(p, A, B, C));
-            const int dx = i - si, dy = j - sj, dz = k - sk;
+            const int dx = ic - si, dy = jc - sj, dz = kc - sk;
             masked = (float)(dx * dx + dy * dy + dz * dz) <= a.mask2;
         }
         // winner record (tracked calls): the coarse source holds a voxel's distance
@@ -341,6 +355,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
         const int slot = pass * 32 + lane;
         const bool mine = slot < nm;
         int lin = 0;
+        int64_t clin = 0;  // coarse voxel of the slot (its flooded seed)
         float3 o = make_float3(0.f, 0.f, 0.f);
         if (mine) {
             // position of the slot-th set bit of the brick mask
@@ -355,6 +370,8 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             const int bit = __ffsll((long long)mm) - 1;
             const int i = bx * BX + bit % BX, j = by * BY + (bit / BX) % BY, k = bz * BZ + bit / (BX * BY);
             lin = (int)(((int64_t)k * a.g.ny + j) * a.g.nx + i);
+            int ic, jc, kc;
+            clin = coarse_index(a, i, j, k, ic, jc, kc);
             o = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
         }
         w.origin[lane] = make_float4(o.x, o.y, o.z, 0.f);
@@ -469,9 +486,9 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             back[lin] = bk;
             bool neg = bk > fr;
             if (fr == bk && a.fallback) {
-                const int32_t s = nearest[lin];
+                const int32_t s = nearest[clin];
                 const int64_t sl2 =
-                    ((int64_t)((s >> 20) & 1023) * a.g.ny + ((s >> 10) & 1023)) * a.g.nx + (s & 1023);
+                    ((int64_t)((s >> 20) & 1023) * a.cny + ((s >> 10) & 1023)) * a.cnx + (s & 1023);
                 float3 A, B, C;
                 load_tri(a.verts, a.V, a.tris, rep_tri[sl2], a.g, A, B, C);
                 const float3 n = cross3(sub3(B, A), sub3(C, A));

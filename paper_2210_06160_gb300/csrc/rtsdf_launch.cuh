@@ -66,7 +66,8 @@ size_t refine_workspace(const rtsdf_grid& g);
 rtsdf_status refine(const rtsdf_grid& g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
                     const void* bvh, const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params& p,
                     uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf, void* ws,
-                    rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, cudaStream_t s);
+                    rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, const rtsdf_grid* coarse,
+                    int ratio, cudaStream_t s);
 
 rtsdf_status shadow(const rtsdf_grid& g, const float* sdf, const float* pos, const float* nrm, int32_t P,
                     const rtsdf_shadow_params& p, float* vis, cudaStream_t s);

@@ -97,6 +97,8 @@ _SIGS = {
                                C.POINTER(RefineParams), _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
     "rtsdf_refine_tracked": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t, _P, _P,
                                        C.POINTER(RefineParams), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
+    "rtsdf_refine_2res": (C.c_int, [C.POINTER(Grid), C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t,
+                                    _P, _P, C.POINTER(RefineParams), _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
     "rtsdf_shadow": (C.c_int, [C.POINTER(Grid), _P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P]),
     "rtsdf_sample": (C.c_int, [C.POINTER(Grid), _P, _P, C.c_int32, _P, _P]),
     "rtsdf_backward_workspace": (C.c_size_t, [C.POINTER(Grid)]),
@@ -259,6 +261,19 @@ def rtsdf_refine_tracked(grid: Grid, verts, tris, bvh, nearest, rep_tri, params:
                                       _stream(stream)), "rtsdf_refine_tracked")
 
 
+def rtsdf_refine_2res(fine: Grid, coarse: Grid, verts, tris, bvh, nearest_c, rep_tri_c, params: RefineParams,
+                      dist_bits, front, back, sdf_out, ws, counters=None, stream=None) -> None:
+    """rtsdf_refine on the fine grid with flooded seeds / representative triangles of the coarse grid."""
+    _check(lib().rtsdf_refine_2res(C.byref(fine), C.byref(coarse), _dev(verts, torch.float32, "verts"),
+                                   verts.shape[0], _dev(tris, torch.int32, "tris"), tris.shape[0],
+                                   _dev(bvh, torch.uint8, "bvh"), bvh.numel(), _dev(nearest_c, torch.int32, "nearest"),
+                                   _dev(rep_tri_c, torch.int32, "rep_tri"), C.byref(params),
+                                   _dev(dist_bits, torch.int32, "dist_bits"), _dev(front, torch.int32, "front"),
+                                   _dev(back, torch.int32, "back"), _dev(sdf_out, torch.float32, "sdf_out"),
+                                   _dev(ws, torch.uint8, "ws"), ws.numel(), _dev(counters, torch.int32, "counters"),
+                                   _stream(stream)), "rtsdf_refine_2res")
+
+
 def rtsdf_sample(grid: Grid, sdf, pts, out, stream=None) -> None:
     _check(lib().rtsdf_sample(C.byref(grid), _dev(sdf, torch.float32, "sdf"), _dev(pts, torch.float32, "pts"),
                               pts.shape[0], _dev(out, torch.float32, "out"), _stream(stream)), "rtsdf_sample")
@@ -373,6 +388,32 @@ class Pipeline:
             out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
         rtsdf_sample(self.g, self.sdf, pts, out, stream)
         return out
+
+
+class TwoResPipeline:
+    """Sec. 2.5.1 two resolutions: voxelize and jump-flood on a coarse grid, resolve and
+    refine on a fine grid over the same box (coarse h = r * fine h)."""
+
+    def __init__(self, fine, coarse, n_verts: int, n_tris: int, device="cuda"):
+        self.coarse = Pipeline(coarse, n_verts, n_tris, device=device)   # seeds, flooding, rep_tri
+        self.fine = Pipeline(fine, n_verts, n_tris, device=device)       # BVH, state, field
+        self.gf, self.gc = make_grid(fine), make_grid(coarse)
+
+    @property
+    def sdf(self):
+        return self.fine.sdf
+
+    def rebuild(self, verts, tris, coarse_steps, params: RefineParams, stream=None):
+        self.coarse.voxelize(verts, tris, stream)
+        self.fine.build_bvh(verts, tris, stream)
+        near = self.coarse.jfa(coarse_steps, stream)
+        f = self.fine
+        rtsdf_refine_2res(self.gf, self.gc, verts, tris, f.bvh, near, self.coarse.rep_tri, params, f.dist_bits,
+                          f.front, f.back, f.sdf, f.ws_refine, f.counters, stream)
+        return f.sdf
+
+    def shadow(self, pos, nrm, params: ShadowParams, vis=None, stream=None):
+        return self.fine.shadow(pos, nrm, params, vis, stream)
 
 
 # ------------------------------------------------------------ differentiation

@@ -515,6 +515,40 @@ def test_refine_converges_with_accumulated_rays(orc):
     assert np.mean(err <= 0.05) >= 0.99
 
 
+def test_resolve_two_resolutions(orc):
+    """Sec. 2.5.1 two resolutions: with ratio 1 the two-grid resolve is the one-grid
+    resolve; with ratio 2 every fine distance is at least the true distance to the
+    mesh (it is a distance to one of its triangles), the fine voxels of a coarse voxel
+    share its mask, and the mask is the integer coarse seed distance."""
+    V, T = scenes.icosphere(2)
+    V = (V * 0.3 + 0.5).astype(np.float32)
+    gf = scenes.Grid(32, 32, 32, (0.0, 0.0, 0.0), 1.0 / 32)
+    vv = orc.to_voxel(V, gf)
+    seed, rep, _ = orc.voxelize(vv, T, gf)
+    near = orc.jfa(gf, seed, scenes.jfa_steps(gf))
+    u1, m1 = orc.resolve(gf, vv, T, near, rep, 3.0)
+    u2, m2 = orc.resolve_2res(gf, gf, 1, vv, T, near, rep, 3.0)
+    np.testing.assert_array_equal(u1, u2)
+    np.testing.assert_array_equal(m1, m2)
+    gc = scenes.Grid(16, 16, 16, (0.0, 0.0, 0.0), 2.0 / 32)
+    vc = orc.to_voxel(V, gc)
+    seed_c, rep_c, _ = orc.voxelize(vc, T, gc)
+    near_c = orc.jfa(gc, seed_c, scenes.jfa_steps(gc))
+    u, m = orc.resolve_2res(gf, gc, 2, vv, T, near_c, rep_c, 1.5)
+    V64 = vv.astype(np.float64)
+    rng = np.random.default_rng(3)
+    for lin in rng.choice(gf.nvox, 300, replace=False):
+        k, j, i = np.unravel_index(lin, gf.shape_zyx)
+        p = np.array([i, j, k]) + 0.5
+        true = min(_tri_dist64(p, *V64[t]) for t in T)
+        assert u.ravel()[lin] >= true - 1e-5
+        s = int(near_c[k // 2, j // 2, i // 2])
+        d2 = (i // 2 - (s & 1023)) ** 2 + (j // 2 - ((s >> 10) & 1023)) ** 2 + (k // 2 - (s >> 20)) ** 2
+        assert m.ravel()[lin] == (d2 <= 2.25)
+    blocks = m.reshape(16, 2, 16, 2, 16, 2)
+    assert np.all(blocks.min(axis=(1, 3, 5)) == blocks.max(axis=(1, 3, 5)))
+
+
 def test_decay_accumulation_closed_form(orc):
     """Eq. (1) (Sec. 2.5.1) without hits is the linear recursion f_t = a f_{t-1} +
     (1 - a) c, whose solution from f_0 = 0 is (1 - a^t) c; with hits the refined value
