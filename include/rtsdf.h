@@ -86,6 +86,9 @@ typedef struct {
     float normal_offset_vox; /* lift of the ray origin along the receiver normal */
     float hit_eps_vox;       /* occluded when sampled distance <= hit_eps */
     float bias_vox;          /* subtracted from every sample (Sec. 2.5.3 thickening) */
+    float jitter_vox;        /* Sec. 2.5.2 jitter: receiver i starts at start_offset + jitter * u_i */
+    uint32_t frame_index;    /* u_i in [0, 1) from Philox4x32-10 on counter (i, frame_index, 0x4A177E2, 0),
+                                key (0x51AD0, 0x7E2): the top 24 bits of the first word times 2^-24 */
 } rtsdf_shadow_params;
 
 /* Device-side counters; each call adds to the fields it owns. */

@@ -70,14 +70,15 @@ def lib():
                 "or_resolve_2res": (None, [G, G, i32, P, P, P, P, f32, f32, P, P]),
                 "or_fine_rep_2res": (None, [G, G, i32, P, P, P]),
                 "or_sample": (None, [G, P, P, i32, P]),
-                "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P]),
+                "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P, P]),
+                "or_jitter_starts": (None, [i32, f32, f32, u32, P]),
                 "or_num_threads": (C.c_int, []),
                 "or_frozen_sources": (None, [G, P, P, P, P, P, P, P, P, P, P, u32, C.c_int, P]),
                 "or_frozen_sdf_f64": (None, [G, P, P, P, C.c_double, P]),
                 "or_frozen_sdf_backward_f64": (None, [G, P, P, P, C.c_double, P, P]),
                 "or_sample_loss_f64": (C.c_double, [G, P, P, i32, P, P]),
                 "or_shadow_loss_f64": (C.c_double, [G, P, P, P, P, i32, P, P, f32, i32, f32, f32, f32, f32, f32,
-                                                    P, P, P]),
+                                                    P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -264,13 +265,22 @@ def rebuild_2res(scene, grid_c, steps_c, frames: int = 1, frame0: int = 0, voxel
                 dist_bits=state[0], front=state[1], back=state[2], sdf=sdf)
 
 
+def jitter_starts(P: int, sp) -> np.ndarray:
+    """First-sample distance of every receiver (Sec. 2.5.2 jitter; start_offset when 0)."""
+    out = np.empty(max(P, 1), dtype=np.float32)
+    lib().or_jitter_starts(int(P), float(sp.start_offset_vox), float(getattr(sp, "jitter_vox", 0.0)),
+                           int(getattr(sp, "frame_index", 0)) & 0xFFFFFFFF, _p(out))
+    return out
+
+
 def shadow(grid, sdf, pos, nrm, sp) -> np.ndarray:
     s, pos, nrm = _f32(sdf), _f32(pos), _f32(nrm)
     L = np.array(sp.light_dir, dtype=np.float32)
     vis = np.empty(len(pos), dtype=np.float32)
+    t0 = jitter_starts(len(pos), sp)
     lib().or_shadow(C.byref(_g(grid)), _p(s), _p(pos), _p(nrm), len(pos), _p(L), float(sp.k),
                     int(sp.steps), float(sp.max_step_vox), float(sp.start_offset_vox),
-                    float(sp.normal_offset_vox), float(sp.hit_eps_vox), float(sp.bias_vox), _p(vis))
+                    float(sp.normal_offset_vox), float(sp.hit_eps_vox), float(sp.bias_vox), _p(t0), _p(vis))
     return vis
 
 
@@ -389,4 +399,5 @@ def shadow_loss_f64(grid, sdf32, sdf64, pos, nrm, light, sp, target, gsdf=None, 
     return float(lib().or_shadow_loss_f64(
         C.byref(_g(grid)), _p(s32), _p(s64), _p(pos), _p(nrm), len(pos), _p(ld), _p(l), float(sp.k), int(sp.steps),
         float(sp.max_step_vox), float(sp.start_offset_vox), float(sp.normal_offset_vox), float(sp.hit_eps_vox),
-        float(sp.bias_vox), _p(target), None if gsdf is None else _p(gsdf), None if gl is None else _p(gl)))
+        float(sp.bias_vox), _p(jitter_starts(len(pos), sp)), _p(target), None if gsdf is None else _p(gsdf),
+        None if gl is None else _p(gl)))

@@ -574,9 +574,24 @@ void or_sample(const or_grid* g, const float* sdf, const float* pts, int32_t M, 
  * Steps are capped at max_step (Sec. 2.5.2); the march starts start_off along
  * the ray from a point lifted normal_off along the normal (Sec. 2.5.3), and the
  * SDF is thickened by bias (Sec. 2.5.3). */
+/* Jittered first-sample distances (Sec. 2.5.2: the ray's offset moves slightly
+ * along the light): t_i = start_off + jitter * u_i, u_i the top 24 bits of the first
+ * word of Philox4x32-10 on counter (i, frame, 0x4A177E2, 0), key (0x51AD0, 0x7E2),
+ * times 2^-24. */
+void or_jitter_starts(int32_t P, float start_off, float jitter, uint32_t frame, float* t_start) {
+    const uint32_t key[2] = {0x51AD0u, 0x7E2u};
+    for (int32_t i = 0; i < P; ++i) {
+        const uint32_t ctr[4] = {(uint32_t)i, frame, 0x4A177E2u, 0u};
+        uint32_t x[4];
+        or_philox4x32_10(ctr, key, x);
+        const float u = (float)(x[0] >> 8) * 0x1p-24f;
+        t_start[i] = jitter == 0.0f ? start_off : start_off + jitter * u;
+    }
+}
+
 void or_shadow(const or_grid* g, const float* sdf, const float* pos, const float* nrm, int32_t P,
                const float light_dir[3], float k, int32_t steps, float max_step, float start_off,
-               float normal_off, float hit_eps, float bias, float* vis) {
+               float normal_off, float hit_eps, float bias, const float* t_start, float* vis) {
     float len = sqrtf(dot3(light_dir, light_dir));
     const float L[3] = {light_dir[0] / len, light_dir[1] / len, light_dir[2] / len};
     const float nxf = (float)g->nx, nyf = (float)g->ny, nzf = (float)g->nz;
@@ -588,7 +603,7 @@ void or_shadow(const or_grid* g, const float* sdf, const float* pos, const float
         org[0] = (x[0] - g->ox) / g->h + normal_off * n[0];
         org[1] = (x[1] - g->oy) / g->h + normal_off * n[1];
         org[2] = (x[2] - g->oz) / g->h + normal_off * n[2];
-        float t = start_off, res = 1.0f, d_prev = INFINITY;
+        float t = t_start ? t_start[pi] : start_off, res = 1.0f, d_prev = INFINITY;
         for (int32_t s = 0; s < steps; ++s) {
             float qx = org[0] + t * L[0], qy = org[1] + t * L[1], qz = org[2] + t * L[2];
             if (qx < 0.0f || qx > nxf || qy < 0.0f || qy > nyf || qz < 0.0f || qz > nzf) break;

@@ -119,7 +119,12 @@ void or_sample(const or_grid* g, const float* sdf, const float* pts, int32_t M, 
  * unit normals) toward a directional light, sphere tracing the SDF (voxel units). */
 void or_shadow(const or_grid* g, const float* sdf, const float* pos, const float* nrm, int32_t P,
                const float light_dir[3], float k, int32_t steps, float max_step, float start_off,
-               float normal_off, float hit_eps, float bias, float* vis);
+               float normal_off, float hit_eps, float bias, const float* t_start, float* vis);
+
+/* Sec. 2.5.2 jitter: per-receiver first-sample distances start_off + jitter * u_i
+ * (u_i from Philox4x32-10 on counter (i, frame, 0x4A177E2, 0), key (0x51AD0, 0x7E2)).
+ * or_shadow and or_shadow_loss_f64 take them in t_start (NULL: start_off). */
+void or_jitter_starts(int32_t P, float start_off, float jitter, uint32_t frame, float* t_start);
 
 /* ------------------------------------------------------------------ adjoint (FP64) */
 
@@ -158,7 +163,7 @@ double or_sample_loss_f64(const or_grid* g, const double* sdf, const float* pts,
 double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sdf, const float* pos,
                           const float* nrm, int32_t P, const float l_decide[3], const double l[3], float k,
                           int32_t steps, float max_step, float start_off, float normal_off, float hit_eps,
-                          float bias, const float* target, double* gsdf, double* gl);
+                          float bias, const float* t_start, const float* target, double* gsdf, double* gl);
 
 /* Helpers for the tests: number of OpenMP threads the oracle uses. */
 int or_num_threads(void);

@@ -274,7 +274,7 @@ double or_sample_loss_f64(const or_grid* g, const double* sdf, const float* pts,
 double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sdf, const float* pos,
                           const float* nrm, int32_t P, const float l_decide[3], const double l[3], float k,
                           int32_t steps, float max_step, float start_off, float normal_off, float hit_eps,
-                          float bias, const float* target, double* gsdf, double* gl) {
+                          float bias, const float* t_start, const float* target, double* gsdf, double* gl) {
     /* FP32 light as the forward normalises it: the control flow comes from there */
     const float lf[3] = {l_decide[0], l_decide[1], l_decide[2]};
     const float lenf = sqrtf(lf[0] * lf[0] + lf[1] * lf[1] + lf[2] * lf[2]);
@@ -292,7 +292,8 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
         org32[0] = (x[0] - g->ox) / g->h + normal_off * n[0];
         org32[1] = (x[1] - g->oy) / g->h + normal_off * n[1];
         org32[2] = (x[2] - g->oz) / g->h + normal_off * n[2];
-        float t32 = start_off, res32 = 1.0f, dprev32 = INFINITY;
+        const float t0 = t_start ? t_start[pi] : start_off;
+        float t32 = t0, res32 = 1.0f, dprev32 = INFINITY;
         int cells[OR_MAX_STEPS][3];
         unsigned char capped[OR_MAX_STEPS];
         int nsteps = 0, argmin = -1, hit = 0;
@@ -334,7 +335,7 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
                                ((double)x[2] - g->oz) / g->h + (double)normal_off * n[2]};
         double tt[OR_MAX_STEPS + 1], dv[OR_MAX_STEPS];
         cell64 cl[OR_MAX_STEPS];
-        tt[0] = start_off;
+        tt[0] = t0;
         for (int s = 0; s <= argmin; ++s) {
             const double q[3] = {org[0] + tt[s] * L[0], org[1] + tt[s] * L[1], org[2] + tt[s] * L[2]};
             cell_of(g, q, cells[s], &cl[s]);

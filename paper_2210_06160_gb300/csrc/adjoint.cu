@@ -101,10 +101,10 @@ __global__ void __launch_bounds__(256) k_sample_adjoint(GridD g, const float* __
 // march of k_shadow operation for operation (so every decision is the forward's),
 // then walks the steps up to the argmin backwards one checkpoint segment at a time.
 // Adds dLoss/d(field) into gsdf and returns dLoss/dL (unit light direction).
-__device__ float3 shadow_pixel_adjoint(const ShadowArgs& a, const float* __restrict__ sdf, float3 o, float gv,
+__device__ float3 shadow_pixel_adjoint(const ShadowArgs& a, const float* __restrict__ sdf, float3 o, float t0, float gv,
                                        float* __restrict__ gsdf) {
     float ck[kMaxCk];
-    float t = a.start_off, res = 1.0f, d_prev = __int_as_float(0x7f800000);
+    float t = t0, res = 1.0f, d_prev = __int_as_float(0x7f800000);
     int argmin = -1;
     bool hit = false, am_tiny = false;
     float am_t = 0.0f, am_d = 0.0f, am_dp = 0.0f, am_y = 0.0f, am_e = 0.0f;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(128) k_shadow_adjoint(ShadowArgs a, const floa
     float3 g = make_float3(0.0f, 0.0f, 0.0f);
     if (i < P) {
         const float gv = __ldg(d_vis + i);
-        if (gv != 0.0f) g = shadow_pixel_adjoint(a, sdf, march_origin(a, pos, nrm, i), gv, gsdf);
+        if (gv != 0.0f) g = shadow_pixel_adjoint(a, sdf, march_origin(a, pos, nrm, i), march_start(a, i), gv, gsdf);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

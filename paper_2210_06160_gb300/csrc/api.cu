@@ -146,7 +146,8 @@ bool shadow_params_ok(const rtsdf_shadow_params* p) {
     if (!p) return false;
     const float* l = p->light_dir;
     const float len2 = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
-    return len2 > 0.0f && isfinite(len2) && p->steps >= 0 && p->max_step_vox > 0.0f && isfinite(p->k);
+    return len2 > 0.0f && isfinite(len2) && p->steps >= 0 && p->max_step_vox > 0.0f && isfinite(p->k) &&
+           p->jitter_vox >= 0.0f && isfinite(p->jitter_vox);
 }
 
 }  // namespace

@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(256) k_shadow(ShadowArgs a, const float* __res
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const float3 o = march_origin(a, pos, nrm, i);
-    float t = a.start_off, res = 1.0f, d_prev = __int_as_float(0x7f800000);
+    float t = march_start(a, i), res = 1.0f, d_prev = __int_as_float(0x7f800000);
     for (int s = 0; s < a.steps; ++s) {
         const float qx = o.x + t * a.L.x, qy = o.y + t * a.L.y, qz = o.z + t * a.L.z;
         if (outside_box(a.g, qx, qy, qz)) break;

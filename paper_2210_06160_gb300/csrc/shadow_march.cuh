@@ -13,6 +13,8 @@ struct ShadowArgs {
     float k;
     int steps;
     float max_step, start_off, normal_off, hit_eps, bias;
+    float jitter;
+    uint32_t frame;
 };
 
 inline ShadowArgs make_shadow_args(const rtsdf_grid& gh, const rtsdf_shadow_params& p) {
@@ -28,7 +30,18 @@ inline ShadowArgs make_shadow_args(const rtsdf_grid& gh, const rtsdf_shadow_para
     a.normal_off = p.normal_offset_vox;
     a.hit_eps = p.hit_eps_vox;
     a.bias = p.bias_vox;
+    a.jitter = p.jitter_vox;
+    a.frame = p.frame_index;
     return a;
+}
+
+// First sample distance of receiver i: start_off, moved along the light by a
+// per-receiver, per-frame jitter (Sec. 2.5.2) drawn from Philox4x32-10.
+__device__ __forceinline__ float march_start(const ShadowArgs& a, int i) {
+    if (a.jitter == 0.0f) return a.start_off;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)i, a.frame, 0x4A177E2u, 0u), 0x51AD0u, 0x7E2u);
+    const float u = (float)(x.x >> 8) * 0x1p-24f;
+    return a.start_off + a.jitter * u;
 }
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return a + (b - a) * t; }

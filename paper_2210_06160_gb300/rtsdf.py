@@ -43,7 +43,8 @@ class RefineParams(C.Structure):
 class ShadowParams(C.Structure):
     _fields_ = [("light_dir", C.c_float * 3), ("k", C.c_float), ("steps", C.c_int32),
                 ("max_step_vox", C.c_float), ("start_offset_vox", C.c_float),
-                ("normal_offset_vox", C.c_float), ("hit_eps_vox", C.c_float), ("bias_vox", C.c_float)]
+                ("normal_offset_vox", C.c_float), ("hit_eps_vox", C.c_float), ("bias_vox", C.c_float),
+                ("jitter_vox", C.c_float), ("frame_index", C.c_uint32)]
 
 
 class Counters(C.Structure):
@@ -174,7 +175,8 @@ def make_refine_params(rp) -> RefineParams:
 def make_shadow_params(sp) -> ShadowParams:
     return ShadowParams((C.c_float * 3)(*[float(v) for v in sp.light_dir]), float(sp.k), int(sp.steps),
                         float(sp.max_step_vox), float(sp.start_offset_vox), float(sp.normal_offset_vox),
-                        float(sp.hit_eps_vox), float(sp.bias_vox))
+                        float(sp.hit_eps_vox), float(sp.bias_vox), float(getattr(sp, "jitter_vox", 0.0)),
+                        int(getattr(sp, "frame_index", 0)) & 0xFFFFFFFF)
 
 
 # ------------------------------------------------------------ size queries

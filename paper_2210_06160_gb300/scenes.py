@@ -190,6 +190,8 @@ class ShadowParams:
     normal_offset_vox: float = 1.0
     hit_eps_vox: float = 0.0
     bias_vox: float = 0.0
+    jitter_vox: float = 0.0        # Sec. 2.5.2 jitter of the first sample along the light
+    frame_index: int = 0
 
 
 def jfa_steps(grid: Grid, extra_one: bool = False) -> list[int]:

@@ -145,9 +145,11 @@ def _compare(ds, light):
     return o, g
 
 
-def test_adjoint_matches_fp64_oracle_miniature():
+@pytest.mark.parametrize("jitter", [0.0, 1.5])
+def test_adjoint_matches_fp64_oracle_miniature(jitter):
     ds = scenes.scene_diff(48, 2, 4, 1, n_samples=4096, shadow_res=64)
-    _compare(ds, (0.3, 1.0, 0.2))
+    sc = dataclasses.replace(ds.scene, shadow=dataclasses.replace(ds.scene.shadow, jitter_vox=jitter, frame_index=3))
+    _compare(dataclasses.replace(ds, scene=sc), (0.3, 1.0, 0.2))
 
 
 def test_adjoint_matches_fp64_oracle_128cube():

@@ -144,7 +144,9 @@ def test_shadow_parity_on_analytic_field():
     nrm = (nrm / np.linalg.norm(nrm, axis=1, keepdims=True)).astype(np.float32)
     for sp in (scenes.ShadowParams(light_dir=(0.3, 1.0, 0.2), k=8.0, steps=96, max_step_vox=1.25),
                scenes.ShadowParams(light_dir=(-0.5, 0.7, 0.1), k=3.0, steps=64, max_step_vox=4.0,
-                                   bias_vox=0.25, hit_eps_vox=0.05, start_offset_vox=0.5)):
+                                   bias_vox=0.25, hit_eps_vox=0.05, start_offset_vox=0.5),
+               scenes.ShadowParams(light_dir=(0.3, 1.0, 0.2), k=8.0, steps=96, max_step_vox=1.25, jitter_vox=1.25,
+                                   frame_index=7)):
         want = oracle.shadow(g, f, pos, nrm, sp)
         got = gpu_shadow(g, f, pos, nrm, sp)
         assert np.abs(got - want).max() <= SHADOW_TOL

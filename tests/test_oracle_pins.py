@@ -13,6 +13,8 @@ import os
 import subprocess
 import sys
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -547,6 +549,33 @@ def test_resolve_two_resolutions(orc):
         assert m.ravel()[lin] == (d2 <= 2.25)
     blocks = m.reshape(16, 2, 16, 2, 16, 2)
     assert np.all(blocks.min(axis=(1, 3, 5)) == blocks.max(axis=(1, 3, 5)))
+
+
+def test_shadow_jitter_starts(orc):
+    """Sec. 2.5.2 jitter: the first-sample distances are start + jitter * u with u
+    uniform on [0, 1) (KS test), different per frame, and exactly start without
+    jitter; a jittered march equals the plain march started at the jittered distance."""
+    from scipy import stats
+    sp = scenes.ShadowParams(start_offset_vox=1.0, jitter_vox=2.0, frame_index=3)
+    t = orc.jitter_starts(20000, sp).astype(np.float64)
+    u = (t - 1.0) / 2.0
+    assert np.all((u >= 0) & (u < 1))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    t2 = orc.jitter_starts(20000, dataclasses.replace(sp, frame_index=4))
+    assert np.mean(t2 != t) > 0.99
+    np.testing.assert_array_equal(orc.jitter_starts(100, dataclasses.replace(sp, jitter_vox=0.0)),
+                                  np.full(100, 1.0, np.float32))
+    # one receiver over a linear field: the jittered march equals a march whose start offset is t_0
+    g = scenes.Grid(20, 40, 20, (0.0, 0.0, 0.0), 1.0)
+    k, j, i = np.meshgrid(*(np.arange(n) + 0.5 for n in (20, 40, 20)), indexing="ij")
+    f = (j - 3.0 + 0.1 * i).astype(np.float32)
+    pos = np.array([[10.0, 5.0, 10.0]], np.float32)
+    nrm = np.array([[0.0, 1.0, 0.0]], np.float32)
+    spj = scenes.ShadowParams(light_dir=(0.2, 1.0, 0.1), k=6.0, steps=32, max_step_vox=2.0, jitter_vox=1.5,
+                              frame_index=9)
+    t0 = float(orc.jitter_starts(1, spj)[0])
+    plain = dataclasses.replace(spj, jitter_vox=0.0, start_offset_vox=t0)
+    assert orc.shadow(g, f, pos, nrm, spj)[0] == orc.shadow(g, f, pos, nrm, plain)[0]
 
 
 def test_decay_accumulation_closed_form(orc):
