@@ -247,6 +247,26 @@ rtsdf_status rtsdf_refine_2res(const rtsdf_grid* fine, const rtsdf_grid* coarse,
 rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm,
                           int32_t P, const rtsdf_shadow_params* p, float* vis, rtsdf_stream stream);
 
+/* ---------------------------------------------------------------- shadow, texture path */
+
+/* The shadow raymarch sampling the field through a 3D texture with hardware
+ * trilinear filtering (Sec. 2.1 notes the 3D-texture grid allows hardware
+ * interpolation).  rtsdf_texture_create allocates the texture's CUDA array (nx*ny*nz
+ * floats) on the current device -- this object, like a batch plan, is owned by the
+ * library and freed by rtsdf_texture_destroy; rtsdf_texture_upload copies a field
+ * (device, x fastest) into it on `stream`.  rtsdf_shadow_tex is rtsdf_shadow with the
+ * texture's field; the texture unit's weights have 8 fractional bits, so samples
+ * differ from the FP32 lerps by up to about 1/256 of the difference between
+ * neighbouring voxels and visibilities differ from rtsdf_shadow's (measured: mean
+ * absolute difference about 4e-5, 99.9% of receivers within 1.3e-3; a receiver whose
+ * hit decision flips can differ by more). */
+typedef struct rtsdf_texture rtsdf_texture;
+rtsdf_status rtsdf_texture_create(const rtsdf_grid* g, rtsdf_texture** tex);
+void rtsdf_texture_destroy(rtsdf_texture* tex);
+rtsdf_status rtsdf_texture_upload(rtsdf_texture* tex, const float* sdf, rtsdf_stream stream);
+rtsdf_status rtsdf_shadow_tex(const rtsdf_texture* tex, const float* pos, const float* nrm, int32_t P,
+                              const rtsdf_shadow_params* p, float* vis, rtsdf_stream stream);
+
 /* ---------------------------------------------------------------- field samples */
 
 /* The field at M world points pts[3m..] (voxel coordinates (p - origin)/h, then

@@ -102,6 +102,10 @@ _SIGS = {
                                     _P, _P, C.POINTER(RefineParams), _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
     "rtsdf_shadow": (C.c_int, [C.POINTER(Grid), _P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P]),
     "rtsdf_sample": (C.c_int, [C.POINTER(Grid), _P, _P, C.c_int32, _P, _P]),
+    "rtsdf_texture_create": (C.c_int, [C.POINTER(Grid), C.POINTER(C.c_void_p)]),
+    "rtsdf_texture_destroy": (None, [_P]),
+    "rtsdf_texture_upload": (C.c_int, [_P, _P, _P]),
+    "rtsdf_shadow_tex": (C.c_int, [_P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P]),
     "rtsdf_backward_workspace": (C.c_size_t, [C.POINTER(Grid)]),
     "rtsdf_backward": (C.c_int, [C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P,
                                  C.POINTER(RefineParams), _P, _P, C.c_int32, _P, _P, _P, C.c_int32,
@@ -390,6 +394,36 @@ class Pipeline:
             out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
         rtsdf_sample(self.g, self.sdf, pts, out, stream)
         return out
+
+
+class SdfTexture:
+    """The field as a 3D texture with hardware trilinear filtering (rtsdf_texture_*)."""
+
+    def __init__(self, grid):
+        self.g = make_grid(grid)
+        self.handle = C.c_void_p()
+        _check(lib().rtsdf_texture_create(C.byref(self.g), C.byref(self.handle)), "rtsdf_texture_create")
+
+    def upload(self, sdf, stream=None):
+        _check(lib().rtsdf_texture_upload(self.handle, _dev(sdf, torch.float32, "sdf"), _stream(stream)),
+               "rtsdf_texture_upload")
+
+    def shadow(self, pos, nrm, params: ShadowParams, vis=None, stream=None):
+        if vis is None:
+            vis = torch.empty(pos.shape[0], dtype=torch.float32, device=pos.device)
+        _check(lib().rtsdf_shadow_tex(self.handle, _dev(pos, torch.float32, "pos"), _dev(nrm, torch.float32, "nrm"),
+                                      pos.shape[0], C.byref(params), _dev(vis, torch.float32, "vis"),
+                                      _stream(stream)), "rtsdf_shadow_tex")
+        return vis
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().rtsdf_texture_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
 
 
 class TwoResPipeline:

@@ -217,3 +217,15 @@ def test_batch_plan_validation(lib):
     b.nsteps = 17
     assert lib.rtsdf_batch_plan_create((BatchScene * 1)(b), 1, C.byref(plan)) == 1
     lib.rtsdf_batch_plan_destroy(None)
+
+
+def test_texture_entry_validation(lib):
+    from paper_2210_06160_gb300.rtsdf import ShadowParams
+    P = C.c_void_p
+    h = C.c_void_p()
+    assert lib.rtsdf_texture_create(C.byref(_grid(0, 8, 8)), C.byref(h)) == 1 and not h.value
+    assert lib.rtsdf_texture_create(C.byref(_grid()), None) == 1
+    sp = ShadowParams((C.c_float * 3)(0, 1, 0), 8.0, 10, 1.0)
+    assert lib.rtsdf_shadow_tex(None, P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
+    assert lib.rtsdf_texture_upload(None, P(FAKE), None) == 1
+    lib.rtsdf_texture_destroy(None)
