@@ -377,11 +377,32 @@ class Pipeline:
                          self.front, self.back, self.sdf, self.ws_refine, self.counters, stream)
         return self.sdf
 
-    def rebuild(self, verts, tris, steps, params: RefineParams, stream=None):
-        self.voxelize(verts, tris, stream)
-        self.build_bvh(verts, tris, stream)
-        self.jfa(steps, stream)
-        return self.refine(verts, tris, params, stream)
+    def rebuild(self, verts, tris, steps, params: RefineParams, stream=None, overlap: bool = True):
+        """One frame: voxelize -> jump flood -> refine; with `overlap` the BVH is built
+        on a second stream while the seeds are voxelized and flooded (the BVH's small
+        kernels leave most of the GPU idle), and the refinement waits for both."""
+        s = torch.cuda.current_stream(self.bvh.device) if stream is None else stream
+        if not overlap:
+            self.voxelize(verts, tris, s)
+            self.build_bvh(verts, tris, s)
+            self.jfa(steps, s)
+            return self.refine(verts, tris, params, s)
+        side = self.side_stream()
+        ready = torch.cuda.Event()
+        ready.record(s)
+        side.wait_event(ready)
+        self.build_bvh(verts, tris, side)
+        built = torch.cuda.Event()
+        built.record(side)
+        self.voxelize(verts, tris, s)
+        self.jfa(steps, s)
+        s.wait_event(built)
+        return self.refine(verts, tris, params, s)
+
+    def side_stream(self):
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(device=self.bvh.device)
+        return self._side
 
     def shadow(self, pos, nrm, params: ShadowParams, vis=None, stream=None):
         if vis is None:
