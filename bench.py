@@ -495,6 +495,8 @@ def run_ours(args):
         return rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f, accumulate=f > 0))
 
     side = P.side_stream()
+    copy = torch.cuda.Stream(device=dev)
+    pending = [None]  # a copy of the previous frame's field and visibility still in flight
 
     def frame(f, ev=None):
         # the BVH builds on a second stream while voxelize + JFA run (Pipeline.rebuild)
@@ -513,6 +515,9 @@ def run_ours(args):
         if ev:
             ev[2].record(stream)
         stream.wait_event(built)
+        if pending[0] is not None:  # the refinement rewrites the field being copied out
+            stream.wait_event(pending[0])
+            pending[0] = None
         P.refine(verts, tris, params(f), stream)
         if ev:
             ev[3].record(stream)
@@ -619,8 +624,17 @@ def run_ours(args):
             verts.copy_(h_verts, non_blocking=True)
             tris.copy_(h_tris, non_blocking=True)
             frame(fi)
-            h_sdf.copy_(P.sdf, non_blocking=True)
-            h_vis.copy_(vis, non_blocking=True)
+            # device -> host copies of the frame's results on a copy stream, overlapping the
+            # next frame's voxelize + BVH + JFA; the next refinement waits for them
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy.wait_event(done)
+            with torch.cuda.stream(copy):
+                h_sdf.copy_(P.sdf, non_blocking=True)
+                h_vis.copy_(vis, non_blocking=True)
+                read = torch.cuda.Event()
+                read.record(copy)
+            pending[0] = read
 
         for _ in range(2):
             e2e_frame(f)
@@ -633,6 +647,8 @@ def run_ours(args):
         for _ in range(ke):
             e2e_frame(f)
             f += 1
+        stream.wait_event(pending[0])
+        pending[0] = None
         e1.record(stream)
         torch.cuda.synchronize()
         te = e0.elapsed_time(e1)
