@@ -63,6 +63,31 @@ def workload_config(sc, workload: str) -> dict:
             "l2": "working set > L2 (grids of 128 MB each); no flush"}
 
 
+# ------------------------------------------------------------------ ranks
+
+def rank_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) from the launcher's environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of every rank's value (the slowest replica's time); no-op alone."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_ms_per_frame(t_max_ms: float, frames_per_rank: int, world: int) -> float:
+    """Whole-job time per frame: every rank rebuilds its own replica (no exchange), so
+    the job does frames_per_rank * world frames in the slowest rank's time."""
+    return t_max_ms / (frames_per_rank * world)
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -163,7 +188,7 @@ def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return
     sc = load_scene(args.workload)
@@ -467,9 +492,7 @@ def run_ours(args):
     from paper_2210_06160_gb300 import build
     from paper_2210_06160_gb300 import rtsdf as rt
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -552,11 +575,7 @@ def run_ours(args):
         dist.barrier()
     launches = rt.rtsdf_kernel_launches() - n_launch0
     clk = clocks.stop()
-    t_ms = start.elapsed_time(end)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(start.elapsed_time(end), world, dev)
     def span(a, b):
         return statistics.mean(evs[i][a].elapsed_time(evs[i][b]) for i in range(args.steps))
 
@@ -565,8 +584,7 @@ def run_ours(args):
     stage = {"voxelize": span(0, 1), "jfa": span(1, 2), "refine": span(2, 3), "shadow": span(3, 4),
              "bvh_side_stream": span(6, 7)}
     ms_per_step = t_ms / args.steps
-    frames_all = args.steps * world
-    value = t_ms / frames_all
+    value = replica_ms_per_frame(t_ms, args.steps, world)
     rebuild_ms = span(0, 3)
     nvox = g.nvox
 
@@ -651,12 +669,8 @@ def run_ours(args):
         pending[0] = None
         e1.record(stream)
         torch.cuda.synchronize()
-        te = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([te], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": te / (ke * world), "unit": "ms/frame",
+        te = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": replica_ms_per_frame(te, ke, world), "unit": "ms/frame",
                "h2d_bytes_per_step": int(h_verts.numel() * 4 + h_tris.numel() * 4),
                "d2h_bytes_per_step": int(h_sdf.numel() * 4 + h_vis.numel() * 4), "steps": ke}
 
