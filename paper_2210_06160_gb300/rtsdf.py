@@ -495,13 +495,13 @@ class SDFShadow(torch.autograd.Function):
         import dataclasses
         sp = dataclasses.replace(shadow, light_dir=tuple(float(v) for v in light.detach().cpu().tolist()))
         verts_c = verts.detach().contiguous()
-        pipe.voxelize(verts_c, tris)
-        pipe.build_bvh(verts_c, tris)
-        pipe.jfa(jfa_steps)
         rparams = None
-        for rp in frames:
+        for f, rp in enumerate(frames):
             rparams = make_refine_params(rp)
-            pipe.refine(verts_c, tris, rparams)
+            if f == 0:
+                pipe.rebuild(verts_c, tris, jfa_steps, rparams)  # BVH overlapped with voxelize + JFA
+            else:
+                pipe.refine(verts_c, tris, rparams)
         samples = pipe.sample(pts)
         vis = pipe.shadow(pos, nrm, make_shadow_params(sp))
         ctx.pipe, ctx.gen = pipe, pipe.generation
