@@ -133,7 +133,7 @@ rtsdf_status refine_checked(const rtsdf_grid* g, const float* verts, int32_t V, 
         return RTSDF_EINVAL;
     if (bvh_bytes_ < bvh_bytes(T)) return RTSDF_ENOMEM;
     if (ws_bytes < refine_workspace(*g)) return RTSDF_ENOMEM;
-    return refine(*g, verts, V, tris, T, bvh, nearest, rep_tri, *p, dist_bits, front, back, sdf_out, ws, counters,
+    return refine(*g, T, bvh, nearest, rep_tri, *p, dist_bits, front, back, sdf_out, ws, counters,
                   win_ray, win_tri, coarse, ratio, cs(stream));
 }
 

@@ -158,8 +158,9 @@ __global__ void k_bbvh_keys(const __grid_constant__ BatchTable t, const float* _
     if (gt >= Ttot) return;
     const int si = RTSDF_FIND_SCENE(t, tri_off, gt);
     const SceneD& S = t.s[si];
-    const uint32_t code =
-        tri_morton(verts + 3 * (int64_t)S.vert_off, S.V, tris + 3 * (int64_t)S.tri_off, gt - S.tri_off, S.g);
+    const uint32_t code = tri_morton(verts + 3 * (int64_t)S.vert_off, S.V, tris + 3 * (int64_t)S.tri_off,
+                                     gt - S.tri_off, S.g,
+                                     reinterpret_cast<TriVox*>(bvh + S.bvh_off + bvh_tris_offset(S.T)));
     if (code != kInvalidKey) atomicAdd(&reinterpret_cast<BvhHeader*>(bvh + S.bvh_off)->n_leaves, 1);
     keys[gt] = ((unsigned long long)si << 32) | code;
     vals[gt] = (uint32_t)gt;
@@ -230,13 +231,10 @@ __global__ void __launch_bounds__(kJX* kJY) k_bjfa_pass(const __grid_constant__ 
 // ------------------------------------------------------------------ coarse field + refine
 
 template <int BX, int BY, int BZ>
-__device__ __forceinline__ RefineArgs scene_args(const SceneD& S, const float* verts, const int32_t* tris,
-                                                 uint32_t frame, int accumulate) {
+__device__ __forceinline__ RefineArgs scene_args(const SceneD& S, const char* bvh, uint32_t frame, int accumulate) {
     RefineArgs a;
     a.g = S.g;
-    a.verts = verts + 3 * (int64_t)S.vert_off;
-    a.V = S.V;
-    a.tris = tris + 3 * (int64_t)S.tri_off;
+    a.tv = reinterpret_cast<const TriVox*>(bvh + S.bvh_off + bvh_tris_offset(S.T));
     a.T = S.T;
     a.mask2 = S.mask2;
     a.beta = S.beta;
@@ -271,6 +269,7 @@ struct BatchGrids {
     float* sdf;
     const float* verts;
     const int32_t* tris;
+    const char* bvh;
 };
 
 template <int BX, int BY, int BZ>
@@ -283,7 +282,7 @@ __global__ void __launch_bounds__(512) k_bresolve(const __grid_constant__ BatchT
     const int local = blockIdx.x - S.tile_start;
     const int gtx = (S.g.nx + 31) / 32, gty = (S.g.ny + 3) / 4;
     const int3 tb = make_int3(local % gtx, (local / gtx) % gty, local / (gtx * gty));
-    const RefineArgs a = scene_args<BX, BY, BZ>(S, G.verts, G.tris, frame, accumulate);
+    const RefineArgs a = scene_args<BX, BY, BZ>(S, G.bvh, frame, accumulate);
     const int64_t o = S.vox_off;
     resolve_tile<BX, BY, BZ>(a, tb, (S.flood_b ? G.buf_b : G.buf_a) + o, G.rep_tri + o, G.dist_bits + o, G.front + o,
                              G.back + o, G.sdf + o, bmask + S.brick_off, blist, count, nullptr, nullptr,
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(kRefineMaxThreads, kRefineWarpsPerSm * 32 / kR
         const uint32_t e = (uint32_t)blist[wk];
         const int si = (int)(e >> kBrickBits), b = (int)(e & ((1u << kBrickBits) - 1u));
         const SceneD& S = t.s[si];
-        const RefineArgs a = scene_args<BX, BY, BZ>(S, G.verts, G.tris, frame, accumulate);
+        const RefineArgs a = scene_args<BX, BY, BZ>(S, G.bvh, frame, accumulate);
         const BvhHeader* hdr = reinterpret_cast<const BvhHeader*>(bvh + S.bvh_off);
         const BvhNode* nodes = reinterpret_cast<const BvhNode*>(bvh + S.bvh_off + bvh_nodes_offset());
         const BvhLeaf* leaves = reinterpret_cast<const BvhLeaf*>(bvh + S.bvh_off + bvh_leaves_offset(S.T));
@@ -528,7 +527,8 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     auto* count = reinterpret_cast<uint32_t*>(ws + P.off_count);
     auto* bmask = reinterpret_cast<unsigned long long*>(ws + P.off_bmask);
     auto* blist = reinterpret_cast<int32_t*>(ws + P.off_blist);
-    BatchGrids G{B.seed, B.buf_b, B.rep_tri, B.dist_bits, B.front, B.back, B.sdf, B.verts, B.tris};
+    BatchGrids G{B.seed, B.buf_b, B.rep_tri, B.dist_bits, B.front, B.back, B.sdf, B.verts, B.tris,
+                 static_cast<const char*>(B.bvh)};
     RTSDF_CUDA(cudaMemsetAsync(count, 0, 16, s));
     k_bresolve<BX, BY, BZ><<<P.ntiles, 512, 0, s>>>(t, G, frame, accumulate, bmask, blist, count);
     RTSDF_LAUNCHED();

@@ -121,10 +121,10 @@ template rtsdf_status radix_sort_pairs<unsigned long long>(unsigned long long*, 
 
 __global__ void k_bvh_keys(const float* __restrict__ verts, int V, const int32_t* __restrict__ tris, int T, GridD g,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, BvhHeader* hdr,
-                           rtsdf_counters* counters) {
+                           TriVox* __restrict__ tv, rtsdf_counters* counters) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
-    const uint32_t key = tri_morton(verts, V, tris, t, g);
+    const uint32_t key = tri_morton(verts, V, tris, t, g, tv);
     if (key != kInvalidKey)
         atomicAdd(&hdr->n_leaves, 1);
     else if (counters)
@@ -189,7 +189,7 @@ static size_t bvh_ws_layout(int32_t T, char* base, BvhWs* w) {
     return off;
 }
 
-size_t bvh_bytes(int32_t T) { return bvh_leaves_offset(T) + sizeof(BvhLeaf) * (size_t)(T > 0 ? T : 1); }
+size_t bvh_bytes(int32_t T) { return bvh_tris_offset(T) + sizeof(TriVox) * (size_t)(T > 0 ? T : 1); }
 size_t bvh_workspace(int32_t T) { return bvh_ws_layout(T, nullptr, nullptr); }
 
 rtsdf_status build_bvh(const float* verts, int32_t V, const int32_t* tris, int32_t T, const rtsdf_grid& gh,
@@ -202,7 +202,8 @@ rtsdf_status build_bvh(const float* verts, int32_t V, const int32_t* tris, int32
     auto* leaves = reinterpret_cast<BvhLeaf*>(static_cast<char*>(bvh) + bvh_leaves_offset(T));
     RTSDF_CUDA(cudaMemsetAsync(hdr, 0, sizeof(BvhHeader), s));
     if (T == 0) return RTSDF_OK;
-    k_bvh_keys<<<(T + 255) / 256, 256, 0, s>>>(verts, V, tris, T, g, w.ka, w.va, hdr, counters);
+    auto* tv = reinterpret_cast<TriVox*>(static_cast<char*>(bvh) + bvh_tris_offset(T));
+    k_bvh_keys<<<(T + 255) / 256, 256, 0, s>>>(verts, V, tris, T, g, w.ka, w.va, hdr, tv, counters);
     RTSDF_LAUNCHED();
     const int ntiles = (T + kSortTile - 1) / kSortTile;
     uint32_t *kin = w.ka, *vin = w.va, *kout = w.kb, *vout = w.vb;

@@ -24,11 +24,14 @@ __device__ __forceinline__ uint32_t spread10(uint32_t x) {
 }
 
 // 30-bit Morton code of triangle t's centroid in the grid box, or kInvalidKey for a
-// triangle every kernel skips (which then sorts after all valid ones).
+// triangle every kernel skips (which then sorts after all valid ones).  Also writes
+// the triangle's voxel-space record tv[t].
 __device__ __forceinline__ uint32_t tri_morton(const float* __restrict__ verts, int V, const int32_t* __restrict__ tris,
-                                               int t, const GridD& g) {
+                                               int t, const GridD& g, TriVox* __restrict__ tv) {
     float3 a, b, c;
-    if (!load_tri(verts, V, tris, t, g, a, b, c)) return kInvalidKey;
+    const bool ok = load_tri(verts, V, tris, t, g, a, b, c);
+    store_tri_vox(tv, t, ok, a, b, c);
+    if (!ok) return kInvalidKey;
     const float scale = 1024.0f / (float)max(g.nx, max(g.ny, g.nz));
     const float cx = (a.x + b.x + c.x) * (1.0f / 3.0f), cy = (a.y + b.y + c.y) * (1.0f / 3.0f),
                 cz = (a.z + b.z + c.z) * (1.0f / 3.0f);

@@ -2,21 +2,23 @@
 //
 //  k_resolve: one thread per voxel, blocks of 32x4x4 voxels = 8 bricks of 4^3.
 //             Coarse distance u_c to the representative triangle of the flooded
-//             seed; unmasked voxels get their final value (u_c - beta); masked
-//             voxels initialise their refine state.  Per brick a 64-bit mask of
-//             its masked voxels is assembled from warp ballots, and bricks with
-//             any masked voxel are appended to a work list.
-//  k_refine:  persistent warp-per-voxel-batch refinement, one 4^3 brick per
-//             64-thread CTA.  Warp 0 walks the BVH once for the whole brick with
-//             the box every ray of the brick stays inside (voxel centres grown
-//             by the ray length) and stages the overlapping triangles in shared
-//             memory; every thread owns one masked voxel and tests its rays
-//             against the staged triangles after a bounding-sphere cull of the
-//             (voxel, triangle) pair.  The closest hit of each ray (ties to the
-//             lower triangle id) lowers the voxel's distance and adds one
-//             front/back vote; the thread then writes the accumulated state and
-//             the signed value.  Staging runs in rounds when a brick has more
-//             candidates than the buffer holds.
+//             seed (read from the BVH's voxel-space triangle table); unmasked
+//             voxels get their final value (u_c - beta); masked voxels initialise
+//             their refine state.  Per brick a 64-bit mask of its masked voxels is
+//             assembled from warp ballots, and bricks with any masked voxel are
+//             appended to a work list.
+//  k_refine:  persistent, one warp per 4^3 brick (two independent warps per
+//             64-thread CTA).  The warp walks the BVH once for the whole brick with
+//             the box every ray of the brick stays inside (voxel centres grown by
+//             the ray length) and stages the overlapping triangles in shared
+//             memory; each lane owns one masked voxel and draws its rays.  The
+//             (voxel, triangle) pairs within reach are compacted and filtered one
+//             per lane against the voxel's rays, and the surviving (voxel, ray,
+//             triangle) items get the exact test 32 at a time.  The closest hit of
+//             each ray (ties to the lower triangle id) lowers the voxel's distance
+//             and adds one front/back vote; the lane then writes the accumulated
+//             state and the signed value.  Staging runs in rounds when a brick has
+//             more candidates than the buffer holds.
 #include "refine_core.cuh"
 #include "rtsdf_launch.cuh"
 
@@ -160,16 +162,12 @@ __global__ void k_refine_report(const uint32_t* __restrict__ count, const unsign
     if (blockIdx.x == 0 && threadIdx.x == 0 && count[2]) atomicAdd(&counters->stack_overflow, count[2]);
 }
 
-rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const int32_t* tris, int32_t T,
-                    const void* bvh, const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params& p,
-                    uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf, void* ws,
+rtsdf_status refine(const rtsdf_grid& gh, int32_t T, const void* bvh, const int32_t* nearest, const int32_t* rep_tri,
+                    const rtsdf_refine_params& p, uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf, void* ws,
                     rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, const rtsdf_grid* coarse,
                     int ratio, cudaStream_t s) {
     RefineArgs a;
     a.g = to_dev(gh);
-    a.verts = verts;
-    a.V = V;
-    a.tris = tris;
     a.T = T;
     a.mask2 = p.mask_vox * p.mask_vox;
     a.beta = p.beta_vox;
@@ -196,6 +194,7 @@ rtsdf_status refine(const rtsdf_grid& gh, const float* verts, int32_t V, const i
     const auto* hdr = static_cast<const BvhHeader*>(bvh);
     const auto* nodes = reinterpret_cast<const BvhNode*>(static_cast<const char*>(bvh) + bvh_nodes_offset());
     const auto* leaves = reinterpret_cast<const BvhLeaf*>(static_cast<const char*>(bvh) + bvh_leaves_offset(T));
+    a.tv = reinterpret_cast<const TriVox*>(static_cast<const char*>(bvh) + bvh_tris_offset(T));
     RTSDF_CUDA(cudaMemsetAsync(w.count, 0, 16, s));
     const dim3 rgrid((gh.nx + 31) / 32, (gh.ny + 3) / 4, (gh.nz + 3) / 4);
     const bool track = win_ray != nullptr;

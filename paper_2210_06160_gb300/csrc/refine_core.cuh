@@ -15,8 +15,7 @@ constexpr int kListCap = 256;        // staged leaves per warp and round
 constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
 constexpr int kNarrowMargin = 96;    // > depth of any tree the builder makes (30-bit codes + 32 index bits)
 constexpr int kRaysPerLane = 8;      // most rays of a voxel per group (one lane per voxel)
-constexpr int kFilterBatch = 2;      // staged triangles filtered per enqueue
-constexpr int kQueueCap = 32 + 32 * 8 * kFilterBatch;  // queued ray/triangle items per warp
+constexpr int kQueueCap = 32 + 32 * kRaysPerLane;    // queued ray/triangle items per warp (< 32 + one round)
 constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
 constexpr int kRefineWarpsPerSm = 20;                 // resident refine warps per SM (shared memory bound)
 
@@ -29,10 +28,8 @@ struct BrickShape {
 
 struct RefineArgs {
     GridD g;
-    const float* verts;
-    int V;
-    const int32_t* tris;
     int T;
+    const TriVox* tv;  // the BVH's voxel-space triangle table (vertices in voxel units)
     float mask2;
     float beta;
     float empty_dist;
@@ -94,7 +91,7 @@ __device__ __forceinline__ void resolve_tile(const RefineArgs& a, int3 tb, const
         }
         float uc = a.empty_dist;
         float3 A, B, C;
-        if (rep >= 0 && load_tri(a.verts, a.V, a.tris, rep, a.g, A, B, C)) {
+        if (rep >= 0 && load_tri_vox(a.tv, a.T, rep, A, B, C)) {
             const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
             uc = sqrtf(closest_d2(p, A, B, C));
             const int dx = ic - si, dy = jc - sj, dz = kc - sk;
@@ -237,12 +234,20 @@ struct WarpSmem {
     int stack[kStackCapW];
     uint32_t queue[kQueueCap];      // (list index << 8) | (slot << 3) | ray
     int qn;                         // queued items
+    uint32_t okm[32];               // rays of each slot that drew a direction
     float4 origin[32];              // voxel centres of the pass's slots
-    float dirx[8][32];              // ray directions of the group, [ray][slot]
-    float diry[8][32];
-    float dirz[8][32];
+    float4 dq[3][2][32];            // ray directions: [component][ray / 4][slot], rays 4q..4q+3 in x..w
+    float4 tsph[32];                // bounding spheres of the chunk's staged triangles
+    float4 tpln[32];                // their planes
+    uint16_t pairs[160];            // (slot << 5) | chunk lane: (voxel, triangle) pairs to filter
     unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
 };
+
+__device__ __forceinline__ float dq_comp(const WarpSmem& w, int comp, int r, int slot) {
+    const float4 q = w.dq[comp][r >> 2][slot];
+    const int e = r & 3;
+    return e == 0 ? q.x : (e == 1 ? q.y : (e == 2 ? q.z : q.w));
+}
 
 // Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
 // closest hit per ray (ties to the lower id) is kept with a 64-bit atomicMin.
@@ -250,7 +255,8 @@ __device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict_
                                          float tmax) {
     const int c = (int)(item >> 8), slot = (int)((item >> 3) & 31u), r = (int)(item & 7u);
     const float4 of = w.origin[slot];
-    const float3 o = make_float3(of.x, of.y, of.z), d = make_float3(w.dirx[r][slot], w.diry[r][slot], w.dirz[r][slot]);
+    const float3 o = make_float3(of.x, of.y, of.z),
+                 d = make_float3(dq_comp(w, 0, r, slot), dq_comp(w, 1, r, slot), dq_comp(w, 2, r, slot));
     const BvhLeaf* L = leaves + w.list[c];
     const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
     const float3 A = make_float3(v0.x, v0.y, v0.z);
@@ -265,25 +271,20 @@ __device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict_
     }
 }
 
-// Which of this lane's rays can hit the triangle of `leaf`: the (voxel, triangle)
-// pair must be within reach of the bounding sphere; each ray's line must pass
-// within rho of the sphere centre with the centre at most rho behind the origin
-// (off the rho-sphere by more than rho*sqrt(2) that is exactly tc >= sqrt(dd -
-// rho^2); nearer, tc >= -rho is kept, a superset); and the ray must cross the
-// triangle's plane at a parameter t_p = sd / dn in [0, tmax], written without a
-// division as |sd - h dn| <= h |dn| (h = tmax / 2) and widened by eps in sd.  All
-// margins exceed the FP32 rounding of both sides, so no triangle the exact test
-// accepts is dropped.
+// Which rays of one (voxel slot v, staged triangle) pair can hit the triangle: each
+// ray's line must pass within rho of the triangle's bounding sphere centre with the
+// centre at most rho behind the origin (off the rho-sphere by more than rho*sqrt(2)
+// that is exactly tc >= sqrt(dd - rho^2); nearer, tc >= -rho is kept, a superset);
+// and the ray must cross the triangle's plane at a parameter t_p = sd / dn in
+// [0, tmax], written without a division as |sd - h dn| <= h |dn| (h = tmax / 2) and
+// widened by eps in sd.  All margins exceed the FP32 rounding of both sides, so no
+// triangle the exact test accepts is dropped.
 template <int RPL>
-__device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf, float3 o, uint32_t okm,
-                                                const float2* dx2, const float2* dy2, const float2* dz2,
-                                                float tmax) {
-    const float4 sph = __ldg(&leaf->sph);
+__device__ __forceinline__ uint32_t filter_pair(const WarpSmem& w, int v, int j, float tmax) {
+    const float4 o = w.origin[v];
+    const float4 sph = w.tsph[j], pl = w.tpln[j];
     const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
     const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
-    const float reach = sph.w + tmax;
-    if (!okm || dd > reach * reach) return 0u;
-    const float4 pl = __ldg(&leaf->pln);
     const float rho = sph.w;
     const float rho2 = rho * rho;
     // v * rsqrt(v) is within a few ulp of sqrt(v) (a few 1e-7 relative), well inside the
@@ -298,28 +299,75 @@ __device__ __forceinline__ uint32_t filter_rays(const BvhLeaf* __restrict__ leaf
     const float2 sd2 = make_float2(sd, sd), mh2 = make_float2(-h, -h);
     uint32_t pm = 0;
 #pragma unroll
-    for (int r = 0; r < RPL / 2; ++r) {
-        const float2 tc = __ffma2_rn(cx2, dx2[r], __ffma2_rn(cy2, dy2[r], __fmul2_rn(cz2, dz2[r])));
-        const float2 dn = __ffma2_rn(nx2, dx2[r], __ffma2_rn(ny2, dy2[r], __fmul2_rn(nz2, dz2[r])));
-        const float2 u = __ffma2_rn(mh2, dn, sd2);  // sd - h dn
-        const bool ok0 = tc.x >= thr && fabsf(u.x) <= __fmaf_rn(h, fabsf(dn.x), eps);
-        const bool ok1 = tc.y >= thr && fabsf(u.y) <= __fmaf_rn(h, fabsf(dn.y), eps);
-        pm |= ((ok0 ? 1u : 0u) << (2 * r)) | ((ok1 ? 1u : 0u) << (2 * r + 1));
+    for (int q = 0; q < (RPL + 3) / 4; ++q) {
+        const float4 qx = w.dq[0][q][v], qy = w.dq[1][q][v], qz = w.dq[2][q][v];
+        const float2 xs[2] = {make_float2(qx.x, qx.y), make_float2(qx.z, qx.w)};
+        const float2 ys[2] = {make_float2(qy.x, qy.y), make_float2(qy.z, qy.w)};
+        const float2 zs[2] = {make_float2(qz.x, qz.y), make_float2(qz.z, qz.w)};
+#pragma unroll
+        for (int hq = 0; hq < (RPL >= 4 ? 2 : 1); ++hq) {
+            const int r = 4 * q + 2 * hq;
+            const float2 tc = __ffma2_rn(cx2, xs[hq], __ffma2_rn(cy2, ys[hq], __fmul2_rn(cz2, zs[hq])));
+            const float2 dn = __ffma2_rn(nx2, xs[hq], __ffma2_rn(ny2, ys[hq], __fmul2_rn(nz2, zs[hq])));
+            const float2 u = __ffma2_rn(mh2, dn, sd2);  // sd - h dn
+            const bool ok0 = tc.x >= thr && fabsf(u.x) <= __fmaf_rn(h, fabsf(dn.x), eps);
+            const bool ok1 = tc.y >= thr && fabsf(u.y) <= __fmaf_rn(h, fabsf(dn.y), eps);
+            pm |= ((ok0 ? 1u : 0u) << r) | ((ok1 ? 1u : 0u) << (r + 1));
+        }
     }
-    return pm & okm;
+    return pm & w.okm[v];
 }
 
+// Exact tests of full batches of 32 queued items.
+__device__ __forceinline__ void run_full_batches(WarpSmem& w, const BvhLeaf* __restrict__ leaves, float tmax) {
+    const int lane = threadIdx.x & 31;
+    int qn = w.qn;
+    if (qn >= 32) {
+        while (qn >= 32) {
+            run_item(w, leaves, w.queue[qn - 32 + lane], tmax);
+            qn -= 32;
+        }
+        __syncwarp();
+        if (lane == 0) w.qn = qn;
+    }
+    __syncwarp();
+}
+
+// Filters one (voxel slot, chunk triangle) pair per lane (lanes >= n idle) and queues
+// the surviving (voxel, ray, triangle) items.
+template <int RPL>
+__device__ __forceinline__ void filter_and_queue(WarpSmem& w, int n, int base, int cb, float tmax) {
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const uint32_t p = w.pairs[base + lane];
+        const int v = (int)(p >> 5), j = (int)(p & 31u);
+        uint32_t pm = filter_pair<RPL>(w, v, j, tmax);
+        if (pm) {
+            int pos = atomicAdd(&w.qn, __popc(pm));
+            while (pm) {
+                const int r = __ffs(pm) - 1;
+                pm &= pm - 1u;
+                w.queue[pos++] = ((uint32_t)(cb + j) << 8) | ((uint32_t)v << 3) | (uint32_t)r;
+            }
+        }
+    }
+    __syncwarp();
+}
 
 // One warp refines one brick (bx, by, bz) whose masked voxels are the set bits of
-// m; lane l owns voxel slot (pass*32 + l) and up to 8 rays of it per group.  For
-// every staged triangle the lane culls the (voxel, triangle) pair by the
-// triangle's bounding sphere grown by the ray length, then each ray by the
-// distance of the sphere's centre to the ray's line (and the side it lies on).
-// Surviving (voxel, ray, triangle) items are queued in shared memory and run
-// through the exact ray/triangle test 32 at a time, so the expensive test does
-// not diverge.  Both filters are conservative (their margins exceed FP32 rounding
-// of the exact test), so they never drop a triangle the exact test accepts; they
-// may use fused multiply-adds because they decide nothing the oracle decides.
+// m; lane l owns voxel slot (pass*32 + l) and draws up to 8 rays of it per group.
+// The brick's staged triangles are taken 32 at a time (one per lane): every
+// (voxel slot, triangle) pair within reach of the triangle's bounding sphere grown
+// by the ray length is compacted into a pair list, four voxels per step, and the
+// pairs are filtered 32 at a time, one per lane, against all rays of the voxel (the
+// line of each ray must pass the sphere, and the ray must cross the triangle's
+// plane within its length).  So the filter does no work for pairs out of reach
+// and none for empty slots of a partly filled pass.  Surviving (voxel, ray,
+// triangle) items are queued in shared memory and run through the exact
+// ray/triangle test 32 at a time, so the expensive test does not diverge.  The
+// filters are conservative (their margins exceed FP32 rounding of the exact test),
+// so they never drop a triangle the exact test accepts; they may use fused
+// multiply-adds because they decide nothing the oracle decides.
 // RPL: rays per lane and group (2, 4 or 8); calls with R <= RPL rays per voxel run
 // one group, so small ray counts do not pay for eight.
 template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane>
@@ -375,6 +423,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             o = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
         }
         w.origin[lane] = make_float4(o.x, o.y, o.z, 0.f);
+        const int nv = min(32, nm - pass * 32);
         uint32_t vbest = 0xffffffffu, vfront = 0, vback = 0;
         // tracked: this call's winning ray, ordered by (t, triangle id), first ray on ties
         unsigned long long wkey = ~0ull;
@@ -393,18 +442,22 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                     else
                         ++n_fail;
                 }
-                w.dirx[r][lane] = dir[r].x;
-                w.diry[r][lane] = dir[r].y;
-                w.dirz[r][lane] = dir[r].z;
                 w.key[r][lane] = ~0ull;
             }
-            float2 dx2[RPL / 2], dy2[RPL / 2], dz2[RPL / 2];
 #pragma unroll
-            for (int r = 0; r < RPL / 2; ++r) {
-                dx2[r] = make_float2(dir[2 * r].x, dir[2 * r + 1].x);
-                dy2[r] = make_float2(dir[2 * r].y, dir[2 * r + 1].y);
-                dz2[r] = make_float2(dir[2 * r].z, dir[2 * r + 1].z);
+            for (int q = 0; q < (RPL + 3) / 4; ++q) {
+                float c[3][4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = 4 * q + e;
+                    c[0][e] = r < RPL ? dir[r < RPL ? r : 0].x : 0.f;
+                    c[1][e] = r < RPL ? dir[r < RPL ? r : 0].y : 0.f;
+                    c[2][e] = r < RPL ? dir[r < RPL ? r : 0].z : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) w.dq[k][q][lane] = make_float4(c[k][0], c[k][1], c[k][2], c[k][3]);
             }
+            w.okm[lane] = okm;
             int sp = 0;
             if (!complete && n_leaves > 0) {
                 if (lane == 0) w.stack[0] = 0;
@@ -419,34 +472,51 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                                                          sp, w.list, 0, overflow);
                 if (lane == 0) w.qn = 0;
                 __syncwarp();
-                for (int c0 = 0; c0 < nc; c0 += kFilterBatch) {
-                    // filter kFilterBatch staged triangles (independent work), then each lane
-                    // that has survivors claims queue slots with one shared atomic
-                    uint32_t pm4 = 0;  // bit (j * 8 + r): ray r vs triangle c0 + j
-#pragma unroll
-                    for (int j = 0; j < kFilterBatch; ++j) {
-                        const int c = c0 + j;
-                        if (c < nc) pm4 |= filter_rays<RPL>(leaves + w.list[c], o, okm, dx2, dy2, dz2, a.tmax) << (8 * j);
+                for (int cb = 0; cb < nc; cb += 32) {
+                    // lane j holds staged triangle cb + j; pairs (voxel slot, j) that pass the
+                    // bounding-sphere reach test are compacted and filtered 32 at a time
+                    const int c = cb + lane;
+                    float4 sph = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float reach2 = -1.0f;
+                    if (c < nc) {
+                        const BvhLeaf* L = leaves + w.list[c];
+                        sph = __ldg(&L->sph);
+                        w.tsph[lane] = sph;
+                        w.tpln[lane] = __ldg(&L->pln);
+                        const float reach = sph.w + a.tmax;
+                        reach2 = reach * reach;
                     }
-                    if (pm4) {
-                        int pos = atomicAdd(&w.qn, __popc(pm4));
-                        while (pm4) {
-                            const int bit = __ffs(pm4) - 1;
-                            pm4 &= pm4 - 1u;
-                            w.queue[pos++] =
-                                ((uint32_t)(c0 + (bit >> 3)) << 8) | ((uint32_t)lane << 3) | (uint32_t)(bit & 7);
+                    __syncwarp();
+                    int np = 0;
+                    const uint32_t lt = (1u << lane) - 1u;
+                    for (int v0 = 0; v0 < nv; v0 += 4) {
+                        bool ok[4];
+                        uint32_t b[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int v = v0 + e;
+                            const float4 ov = w.origin[v & 31];
+                            const float dcx = sph.x - ov.x, dcy = sph.y - ov.y, dcz = sph.z - ov.z;
+                            const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
+                            ok[e] = v < nv && dd <= reach2;
+                            b[e] = __ballot_sync(0xffffffffu, ok[e]);
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (ok[e]) w.pairs[np + __popc(b[e] & lt)] = (uint16_t)(((v0 + e) << 5) | lane);
+                            np += __popc(b[e]);
+                        }
+                        while (np >= 32) {
+                            __syncwarp();
+                            np -= 32;
+                            filter_and_queue<RPL>(w, 32, np, cb, a.tmax);
+                            run_full_batches(w, leaves, a.tmax);
                         }
                     }
                     __syncwarp();
-                    int qn = w.qn;
-                    if (qn >= 32) {
-                        while (qn >= 32) {
-                            run_item(w, leaves, w.queue[qn - 32 + lane], a.tmax);
-                            qn -= 32;
-                        }
-                        __syncwarp();
-                        if (lane == 0) w.qn = qn;
-                        __syncwarp();
+                    if (np > 0) {
+                        filter_and_queue<RPL>(w, np, 0, cb, a.tmax);
+                        run_full_batches(w, leaves, a.tmax);
                     }
                 }
                 {
@@ -489,8 +559,8 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                 const int32_t s = nearest[clin];
                 const int64_t sl2 =
                     ((int64_t)((s >> 20) & 1023) * a.cny + ((s >> 10) & 1023)) * a.cnx + (s & 1023);
-                float3 A, B, C;
-                load_tri(a.verts, a.V, a.tris, rep_tri[sl2], a.g, A, B, C);
+                float3 A = make_float3(0.f, 0.f, 0.f), B = A, C = A;
+                load_tri_vox(a.tv, a.T, rep_tri[sl2], A, B, C);
                 const float3 n = cross3(sub3(B, A), sub3(C, A));
                 neg = dot3(sub3(o, A), n) < 0.0f;
             }

@@ -240,9 +240,39 @@ struct alignas(16) BvhLeaf {
     float4 pln;  // unit normal xyz (0 for a degenerate triangle), w = normal . A
 };
 
+// Triangle t in voxel coordinates, indexed by triangle id (not in tree order): the
+// vertices exactly as load_tri computes them, written once per build so that the
+// per-voxel passes (coarse distance, sign fallback) read one 48-byte record instead
+// of the index triple, three vertices and nine divisions.  a.w = 1 for a valid
+// triangle, 0 for one that every kernel skips.
+struct alignas(16) TriVox {
+    float4 a, b, c;
+};
+
 __host__ __device__ inline size_t bvh_nodes_offset() { return sizeof(BvhHeader); }
 __host__ __device__ inline size_t bvh_leaves_offset(int32_t T) {
     return sizeof(BvhHeader) + sizeof(BvhNode) * (size_t)(T > 1 ? T - 1 : 1);
+}
+__host__ __device__ inline size_t bvh_tris_offset(int32_t T) {
+    return bvh_leaves_offset(T) + sizeof(BvhLeaf) * (size_t)(T > 0 ? T : 1);
+}
+
+__device__ __forceinline__ void store_tri_vox(TriVox* __restrict__ tv, int t, bool ok, float3 a, float3 b, float3 c) {
+    tv[t] = ok ? TriVox{make_float4(a.x, a.y, a.z, 1.0f), make_float4(b.x, b.y, b.z, 0.0f),
+                        make_float4(c.x, c.y, c.z, 0.0f)}
+               : TriVox{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                        make_float4(0.f, 0.f, 0.f, 0.f)};
+}
+
+// Triangle t from the table; false for an id out of [0, T) or an invalid triangle.
+__device__ __forceinline__ bool load_tri_vox(const TriVox* __restrict__ tv, int T, int t, float3& a, float3& b,
+                                             float3& c) {
+    if (t < 0 || t >= T) return false;
+    const float4 fa = __ldg(&tv[t].a), fb = __ldg(&tv[t].b), fc = __ldg(&tv[t].c);
+    a = make_float3(fa.x, fa.y, fa.z);
+    b = make_float3(fb.x, fb.y, fb.z);
+    c = make_float3(fc.x, fc.y, fc.z);
+    return fa.w != 0.0f;
 }
 
 // ------------------------------------------------------------------ misc

@@ -63,8 +63,7 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
                  int32_t** result, cudaStream_t s);
 
 size_t refine_workspace(const rtsdf_grid& g);
-rtsdf_status refine(const rtsdf_grid& g, const float* verts, int32_t V, const int32_t* tris, int32_t T,
-                    const void* bvh, const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params& p,
+rtsdf_status refine(const rtsdf_grid& g, int32_t T, const void* bvh, const int32_t* nearest, const int32_t* rep_tri, const rtsdf_refine_params& p,
                     uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf, void* ws,
                     rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri, const rtsdf_grid* coarse,
                     int ratio, cudaStream_t s);
