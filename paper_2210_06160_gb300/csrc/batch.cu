@@ -273,7 +273,7 @@ struct BatchGrids {
 };
 
 template <int BX, int BY, int BZ>
-__global__ void __launch_bounds__(512) k_bresolve(const __grid_constant__ BatchTable t, BatchGrids G, uint32_t frame,
+__global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ BatchTable t, BatchGrids G, uint32_t frame,
                                                   int accumulate, unsigned long long* __restrict__ bmask,
                                                   int32_t* __restrict__ blist, uint32_t* __restrict__ count) {
     __shared__ unsigned long long smask[kMaxBricksPerTile];

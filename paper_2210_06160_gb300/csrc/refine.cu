@@ -60,7 +60,9 @@ size_t refine_workspace(const rtsdf_grid& g) { return refine_ws_layout(g, nullpt
 
 // ------------------------------------------------------------------ resolve
 
-__global__ void __launch_bounds__(512) k_resolve(RefineArgs a, const int32_t* __restrict__ nearest,
+// Latency-bound (a chain of dependent loads per voxel: flooded seed, representative
+// triangle, its record), so it is built for four resident 512-thread blocks per SM.
+__global__ void __launch_bounds__(512, 4) k_resolve(RefineArgs a, const int32_t* __restrict__ nearest,
                                                  const int32_t* __restrict__ rep_tri,
                                                  uint32_t* __restrict__ dist_bits, uint32_t* __restrict__ front,
                                                  uint32_t* __restrict__ back, float* __restrict__ sdf,

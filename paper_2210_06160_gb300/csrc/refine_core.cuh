@@ -243,10 +243,9 @@ struct WarpSmem {
     unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
 };
 
+// Component comp of ray r's direction at a slot (one scalar shared-memory load).
 __device__ __forceinline__ float dq_comp(const WarpSmem& w, int comp, int r, int slot) {
-    const float4 q = w.dq[comp][r >> 2][slot];
-    const int e = r & 3;
-    return e == 0 ? q.x : (e == 1 ? q.y : (e == 2 ? q.z : q.w));
+    return reinterpret_cast<const float*>(&w.dq[comp][r >> 2][slot])[r & 3];
 }
 
 // Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
