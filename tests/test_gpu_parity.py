@@ -75,6 +75,37 @@ def test_random_triangles_ragged_grid_parity(R):
     assert got["counters"]["skipped_triangles"] == 2 * 2  # voxelize + BVH each count both
 
 
+def _dense_cluster_scene(R: int, n: int = 3000):
+    """n small triangles packed in a ball of radius 2.5 voxels: every brick near it
+    reaches far more triangles than one staging round of the refine walk holds."""
+    rng = np.random.default_rng(21)
+    g = scenes.Grid(24, 24, 24, (0.0, 0.0, 0.0), 1.0 / 24)
+    u = rng.normal(size=(n, 3))
+    c = 12.0 + u / np.linalg.norm(u, axis=1, keepdims=True) * 2.5 * rng.uniform(0, 1, (n, 1)) ** (1 / 3)
+    tri = (c[:, None, :] + rng.normal(0, 0.3, (n, 3, 3))) * g.h
+    V = tri.reshape(-1, 3).astype(np.float32)
+    T = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    rp = scenes.RefineParams(mask_vox=3.0, rays_per_voxel=R, max_ray_vox=6.0, beta_vox=1.0, key=(7, 9))
+    return scenes.Scene("cluster", V, T, g, rp, scenes.ShadowParams(steps=30, max_step_vox=2.0),
+                        scenes.jfa_steps(g), 1, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+
+
+@pytest.mark.parametrize("R", [4, 16])
+def test_dense_cluster_staging_rounds_parity(R):
+    """Bricks whose candidate triangles overflow the staging list (the walk resumes
+    in rounds, per pass and per ray group), bit-exact against the oracle's brute force."""
+    sc = _dense_cluster_scene(R)
+    vv = sc.verts.astype(np.float64).reshape(-1, 3, 3) / sc.grid.h
+    lo, hi = vv.min(axis=1), vv.max(axis=1)
+    qlo = np.array([8.5, 8.5, 8.5])  # the brick at (2, 2, 2): voxel centres 8.5 .. 11.5
+    gap = np.maximum(np.maximum(lo - (qlo + 3.0), qlo - hi), 0.0)
+    assert int(((gap ** 2).sum(1) <= 36.0).sum()) > 2 * 256  # several staging rounds for that brick
+    ref = oracle.rebuild(sc)
+    got, _ = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    assert got["counters"]["stack_overflow"] == 0 and got["counters"]["rays_hit"] > 0
+
+
 def test_jfa_random_seeds_and_shapes_parity():
     rng = np.random.default_rng(1)
     for dims in [(1, 1, 1), (2, 3, 1), (33, 17, 65), (1023, 2, 3), (64, 64, 64)]:
