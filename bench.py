@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SDF rebuild ms/frame @400x200x400, GVoxel/s, %HBM roof; bwd+batch vs plain"
 JFA_ROOM_DRAM_BYTES_PER_FRAME = 2_206_969_088
+# smsp__inst_executed.sum of k_refine for one room frame (8 rays, 7.24 M masked voxels), from one
+# ncu capture of this kernel version; the refine kernel is bound by instruction issue, not bytes
+REFINE_ROOM_WARP_INSTR_PER_FRAME = 4_006_479_809
 
 
 def parse():
@@ -604,6 +607,21 @@ def run_ours(args):
                 "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes,
                 "limit": "integer ALU and FMA-heavy pipes (half-rate), not HBM"}
 
+    # the dominant kernel by time, k_refine, is issue-bound: warp-instructions per second against
+    # four schedulers per SM at the sampled SM clock; timed by the refine stage, which also holds
+    # k_resolve and k_refine_report, so the rate is a lower bound on k_refine's own
+    roofline_refine = None
+    if args.workload == "room":
+        sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = 4.0 * nsm * sm_mhz * 1e6 / 1e9
+        issue_rate = REFINE_ROOM_WARP_INSTR_PER_FRAME / (stage["refine"] * 1e-3) / 1e9
+        roofline_refine = {"kernel": "k_refine (timed with k_resolve in the refine stage)", "bound": "issue",
+                           "achieved": round(issue_rate, 1), "peak": round(issue_peak, 1),
+                           "unit": "G warp-instructions/s", "frac": round(issue_rate / issue_peak, 4),
+                           "warp_instructions_per_frame": REFINE_ROOM_WARP_INSTR_PER_FRAME,
+                           "peak_source": f"4 schedulers x {nsm} SMs x median SM clock {sm_mhz:.0f} MHz"}
+
     counters = rt.counters_dict(P.counters)
 
     # the shadow through the texture path on the last frame's field (not part of the frame)
@@ -693,7 +711,7 @@ def run_ours(args):
                 "gvoxel_per_s": round(nvox / (rebuild_ms * 1e-3) / 1e9, 3),
                 "rebuild_ms": round(rebuild_ms, 4),
                 "stage_ms": {k: round(v, 4) for k, v in stage.items()},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline, "roofline_refine": roofline_refine, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "backward": bwd, "batch": batch, "dynamic": dyn, "two_resolution": two, "shadow_texture": tex,
                 "clocks": clk, "counters": counters, "impl": "ours"}
         print(json.dumps(line), flush=True)
