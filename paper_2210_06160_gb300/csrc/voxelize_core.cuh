@@ -35,13 +35,42 @@ __device__ __forceinline__ uint32_t range_bricks(const TriRange& r) {
                       (r.hi[2] / kBrick - r.lo[2] / kBrick + 1));
 }
 
+// Voxel test of one voxel: closed-cube SAT overlap, then the 64-bit key (closest-point
+// distance^2 bits, triangle id) lowered with atomicMin.
+__device__ __forceinline__ void vox_voxel(float3 a, float3 b, float3 c, int i, int j, int k, int tri_id,
+                                          const GridD& g, unsigned long long* __restrict__ keys) {
+    const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
+    if (!tri_box_overlap(a, b, c, p, 0.5f)) return;
+    const float d2 = closest_d2(p, a, b, c);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned long long)(uint32_t)tri_id;
+    const int64_t lin = ((int64_t)k * g.ny + j) * g.nx + i;
+    atomicMin(keys + lin, key);
+}
+
+// Position of the n-th (0-based) set bit of a 16-bit mask holding more than n set bits.
+__device__ __forceinline__ int nth_set_bit16(uint32_t x, int n) {
+    int pos = 0;
+    int c = __popc(x & 0xFFu);
+    if (n >= c) { n -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xFu);
+    if (n >= c) { n -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (n >= c) { n -= c; x >>= 2; pos += 2; }
+    if (n >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
+
 // The voxel tests of one (triangle, brick) item: a warp culls the brick (enlarged
 // by a margin far above FP32 rounding of the voxel test), then its lanes test the
-// voxels of brick ∩ range and lower each overlapped voxel's 64-bit key
-// (closest-point distance^2 bits, triangle id) with atomicMin.
+// voxels of brick ∩ range.  When that sub-box is large (a big triangle, typically a
+// slanted plane through its whole bounding box), the voxels whose centres lie
+// farther from the triangle's plane than the cube's half-extent along the normal
+// (plus 0.02 voxel, far above the FP32 rounding of the separating-axis test on the
+// plane axis, which rejects them anyway) are dropped first, and the remaining ones
+// are compacted over the warp, so the full test runs on dense lanes.
 __device__ __forceinline__ void vox_item(float3 a, float3 b, float3 c, const TriRange& r, int local, int tri_id,
                                          const GridD& g, unsigned long long* __restrict__ keys) {
-    const uint32_t lane = lane_id();
+    const int lane = (int)lane_id();
     const int nbx = r.hi[0] / kBrick - r.lo[0] / kBrick + 1;
     const int nby = r.hi[1] / kBrick - r.lo[1] / kBrick + 1;
     const int bx = r.lo[0] / kBrick + local % nbx;
@@ -54,15 +83,53 @@ __device__ __forceinline__ void vox_item(float3 a, float3 b, float3 c, const Tri
     const int y0 = max(r.lo[1], by * kBrick), y1 = min(r.hi[1], by * kBrick + kBrick - 1);
     const int z0 = max(r.lo[2], bz * kBrick), z1 = min(r.hi[2], bz * kBrick + kBrick - 1);
     const int sx = x1 - x0 + 1, sy = y1 - y0 + 1, nsub = sx * sy * (z1 - z0 + 1);
-    for (int v = (int)lane; v < nsub; v += kWarp) {
-        const int i = x0 + v % sx, j = y0 + (v / sx) % sy, k = z0 + v / (sx * sy);
-        const float3 p = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
-        if (!tri_box_overlap(a, b, c, p, 0.5f)) continue;
-        const float d2 = closest_d2(p, a, b, c);
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned long long)(uint32_t)tri_id;
-        const int64_t lin = ((int64_t)k * g.ny + j) * g.nx + i;
-        atomicMin(keys + lin, key);
+    const float3 e1 = sub3(b, a), e2 = sub3(c, a);
+    const float3 nn = cross3(e1, e2);
+    const float len2 = dot3(nn, nn);
+    if (nsub <= 2 * kWarp || !(len2 > 0.0f) || !isfinite(len2)) {
+        for (int v = lane; v < nsub; v += kWarp)
+            vox_voxel(a, b, c, x0 + v % sx, y0 + (v / sx) % sy, z0 + v / (sx * sy), tri_id, g, keys);
+        return;
+    }
+    const float inv = rsqrtf(len2);
+    const float3 nu = make_float3(nn.x * inv, nn.y * inv, nn.z * inv);
+    const float reach = 0.5f * (fabsf(nu.x) + fabsf(nu.y) + fabsf(nu.z)) + 0.02f;
+    // slots of the 8^3 brick, x fastest; lane l holds slots l + 32 it (it < 16)
+    static_assert(kBrick == 8, "slot layout assumes 8^3 bricks");
+    uint32_t m = 0;
+#pragma unroll 4
+    for (int it = 0; it < 16; ++it) {
+        const int v = lane + kWarp * it;
+        const int i = bx * kBrick + (v & 7), j = by * kBrick + ((v >> 3) & 7), k = bz * kBrick + (v >> 6);
+        if (i < x0 || i > x1 || j < y0 || j > y1 || k < z0 || k > z1) continue;
+        const float dist = nu.x * ((float)i + 0.5f - a.x) + nu.y * ((float)j + 0.5f - a.y) +
+                           nu.z * ((float)k + 0.5f - a.z);
+        if (fabsf(dist) <= reach) m |= 1u << it;
+    }
+    const int cnt = __popc(m);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < kWarp; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+    const int excl = incl - cnt;
+    for (int base = 0; base < total; base += kWarp) {
+        const int q = base + lane;
+        int owner = 0;  // last lane whose exclusive count is <= q
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, owner + step);
+            if (e <= q) owner += step;
+        }
+        const uint32_t mo = __shfl_sync(0xffffffffu, m, owner);
+        const int eo = __shfl_sync(0xffffffffu, excl, owner);
+        if (q < total) {
+            const int v = owner + kWarp * nth_set_bit16(mo, q - eo);
+            vox_voxel(a, b, c, bx * kBrick + (v & 7), by * kBrick + ((v >> 3) & 7), bz * kBrick + (v >> 6), tri_id, g,
+                      keys);
+        }
     }
 }
 
