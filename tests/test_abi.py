@@ -74,6 +74,16 @@ def test_pointer_and_size_validation(lib):
                                lib.rtsdf_bvh_workspace(T), None, None) == 2
 
 
+def test_bvh_buffer_holds_tree_leaves_and_triangle_table(lib):
+    """The BVH buffer grows linearly in T: per triangle at least an inner node (64 B), a leaf (80 B)
+    and a voxel-space triangle record (48 B), plus a fixed header."""
+    sizes = [lib.rtsdf_bvh_bytes(T) for T in (1, 1000, 2000, 100_000)]
+    assert sizes[0] > 0
+    assert sizes[2] - sizes[1] == 1000 * (64 + 80 + 48)
+    assert sizes[3] >= 100_000 * (64 + 80 + 48)
+    assert lib.rtsdf_bvh_bytes(-1) == 0
+
+
 def test_jfa_validation(lib):
     g = _grid()
     P = C.c_void_p
