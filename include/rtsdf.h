@@ -128,8 +128,10 @@ size_t rtsdf_bvh_workspace(int32_t T);
  * paper uses the driver-built DXR structure, Sec. 2 and 3.5.1): linear BVH from
  * 30-bit Morton codes of triangle centroids in the grid box, radix-sorted, with
  * Karras' (HPG 2012) radix-tree topology and bottom-up conservative boxes.  The
- * buffer is self-contained (leaves hold voxel-space triangles) and only
- * meaningful to rtsdf_refine with the same grid. */
+ * buffer is self-contained (leaves hold voxel-space triangles for the ray tests,
+ * and a table indexed by triangle id holds each triangle's voxel-space vertices,
+ * which rtsdf_refine's coarse distance and sign fallback read) and only
+ * meaningful to rtsdf_refine with the same mesh and grid. */
 rtsdf_status rtsdf_build_bvh(const float* verts, int32_t V, const int32_t* tris, int32_t T,
                              const rtsdf_grid* g, void* bvh, size_t bvh_bytes,
                              void* ws, size_t ws_bytes, rtsdf_counters* counters, rtsdf_stream stream);
