@@ -65,9 +65,11 @@ __device__ __forceinline__ int nth_set_bit16(uint32_t x, int n) {
 // voxels of brick ∩ range.  When that sub-box is large (a big triangle, typically a
 // slanted plane through its whole bounding box), the voxels whose centres lie
 // farther from the triangle's plane than the cube's half-extent along the normal
-// (plus 0.02 voxel, far above the FP32 rounding of the separating-axis test on the
-// plane axis, which rejects them anyway) are dropped first, and the remaining ones
-// are compacted over the warp, so the full test runs on dense lanes.
+// (a cube that meets the triangle meets its plane) are dropped first, and the
+// remaining ones are compacted over the warp, so the full test runs on dense
+// lanes.  The margin (0.02 voxel, above the FP32 rounding of the separating-axis
+// test, plus the computed normal's angular error times the distance) keeps every
+// voxel that test can accept.
 __device__ __forceinline__ void vox_item(float3 a, float3 b, float3 c, const TriRange& r, int local, int tri_id,
                                          const GridD& g, unsigned long long* __restrict__ keys) {
     const int lane = (int)lane_id();
@@ -86,14 +88,21 @@ __device__ __forceinline__ void vox_item(float3 a, float3 b, float3 c, const Tri
     const float3 e1 = sub3(b, a), e2 = sub3(c, a);
     const float3 nn = cross3(e1, e2);
     const float len2 = dot3(nn, nn);
-    if (nsub <= 2 * kWarp || !(len2 > 0.0f) || !isfinite(len2)) {
+    // sin^2 of the angle between the edges; the computed unit normal is off the true one by at
+    // most about 8u/sin + 8u radians (u = 2^-24), which the margin below scales by the distance
+    // from vertex a to the brick's voxels; slivers (sin < 1e-4) skip the filter
+    const float sin2 = len2 / (dot3(e1, e1) * dot3(e2, e2));
+    if (nsub <= 2 * kWarp || !(sin2 > 1e-8f) || !isfinite(len2)) {
         for (int v = lane; v < nsub; v += kWarp)
             vox_voxel(a, b, c, x0 + v % sx, y0 + (v / sx) % sy, z0 + v / (sx * sy), tri_id, g, keys);
         return;
     }
     const float inv = rsqrtf(len2);
     const float3 nu = make_float3(nn.x * inv, nn.y * inv, nn.z * inv);
-    const float reach = 0.5f * (fabsf(nu.x) + fabsf(nu.y) + fabsf(nu.z)) + 0.02f;
+    const float3 da = sub3(bc, a);
+    const float span = sqrtf(dot3(da, da)) + 7.0f;  // >= |voxel centre - a| over the brick
+    const float ang = 0x1p-21f * rsqrtf(sin2) + 0x1p-20f;  // 8u / sin + 16u, with room for the dot product
+    const float reach = 0.5f * (fabsf(nu.x) + fabsf(nu.y) + fabsf(nu.z)) + 0.02f + ang * span;
     // slots of the 8^3 brick, x fastest; lane l holds slots l + 32 it (it < 16)
     static_assert(kBrick == 8, "slot layout assumes 8^3 bricks");
     uint32_t m = 0;

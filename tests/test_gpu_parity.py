@@ -106,6 +106,40 @@ def test_dense_cluster_staging_rounds_parity(R):
     assert got["counters"]["stack_overflow"] == 0 and got["counters"]["rays_hit"] > 0
 
 
+def test_voxelize_big_and_sliver_triangles_bit_exact():
+    """Long triangles at random orientations, from well shaped to slivers (sine of the
+    angle between edges 0.5 down to 1e-5), spanning many bricks: seeds and representative
+    triangles bit-exact against the oracle (the big-triangle plane filter must keep
+    every voxel the separating-axis test accepts)."""
+    rng = np.random.default_rng(31)
+    g = scenes.Grid(64, 48, 40, (0.0, 0.0, 0.0), 0.05)
+    dims = np.array([64, 48, 40], np.float64)
+    tris = []
+    for sin in (0.5, 1e-2, 1e-3, 2e-4, 5e-5, 1e-5):
+        for _ in range(12):
+            a = rng.uniform(0.1, 0.9, 3) * dims
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            q = rng.normal(size=3)
+            q -= d * (q @ d)
+            q /= np.linalg.norm(q)
+            L = rng.uniform(20.0, 45.0)
+            b = a + d * L
+            c = a + d * L * rng.uniform(0.2, 0.8) + q * L * sin
+            tris.append([a, b, c])
+    V = (np.array(tris).reshape(-1, 3) * g.h).astype(np.float32)
+    T = np.arange(len(V), dtype=np.int32).reshape(-1, 3)
+    want_seed, want_rep, _ = oracle.voxelize(oracle.to_voxel(V, g), T, g)
+    gg = rt.make_grid(g)
+    seed = torch.empty(g.shape_zyx, dtype=torch.int32, device="cuda")
+    rep = torch.empty_like(seed)
+    ws = torch.empty(rt.rtsdf_voxelize_workspace(len(T), gg), dtype=torch.uint8, device="cuda")
+    rt.rtsdf_voxelize(to_dev(V), to_dev(T), gg, seed, rep, ws)
+    assert int((want_seed != -1).sum()) > 1000
+    np.testing.assert_array_equal(seed.cpu().numpy(), want_seed)
+    np.testing.assert_array_equal(rep.cpu().numpy(), want_rep)
+
+
 def test_jfa_random_seeds_and_shapes_parity():
     rng = np.random.default_rng(1)
     for dims in [(1, 1, 1), (2, 3, 1), (33, 17, 65), (1023, 2, 3), (64, 64, 64)]:
