@@ -36,14 +36,17 @@ constexpr int kChunk = 16;        // outputs per column and block along z
 // (up to) three outputs p-1, p, p+1 that read it, so every output voxel costs
 // nine tap loads instead of 27.  Output p is complete once plane p+1 is in.
 //
-// Columns whose 3x3 tap columns lie inside the grid take a specialised path for
-// power-of-two offsets (offset K known at compile time, so the nine taps of a plane
-// are three row pointers with immediate offsets).  It folds the empty marker into
-// the arithmetic instead of branching on it: 0xFFFFFFFF decodes to the seed
-// (1023, 1023, 4095), whose squared distance from any voxel of a grid with
-// dimensions <= 1023 exceeds 3070^2 > 3 * 1023^2, more than any real seed's, so it
-// never wins against one and is the result (the empty marker) only when every tap
-// is empty.  The candidate (d', s) is one signed 64-bit key, d' in the high word,
+// Power-of-two offsets (offset K known at compile time) take specialised paths:
+// columns whose 3x3 tap columns lie inside the grid read the nine taps of a plane
+// through three row pointers with immediate offsets; columns near the x/y faces
+// read only the tap rows inside the grid (1, 2 or 3, warp-uniform) and clamp a
+// missing left/right tap to their own column (jfa_column_band).  Only other
+// offsets take the bounds-checked generic path.  The specialised paths fold the
+// empty marker into the arithmetic instead of branching on it: 0xFFFFFFFF decodes
+// to the seed (1023, 1023, 4095), whose squared distance from any voxel of a grid
+// with dimensions <= 1023 exceeds 3070^2 > 3 * 1023^2, more than any real seed's,
+// so it never wins against one and is the result (the empty marker) only when
+// every tap is empty.  The candidate (d', s) is one signed 64-bit key, d' in the high word,
 // so the lexicographic argmin is a 64-bit minimum.
 //
 // The pass is bound by the integer ALU pipe (compares, selects, shifts and masks
@@ -99,7 +102,64 @@ __device__ __forceinline__ void jfa_column_interior(const uint32_t* __restrict__
     }
 }
 
-// Any column, any offset: bounds-checked taps, empty taps skipped.
+// Power-of-two offset, columns near the grid's x/y faces: only the NR tap rows
+// dy0 .. dy0+NR-1 lie inside the grid (warp-uniform: they depend on y only), and a
+// lane whose left or right tap column is outside loads its own column there
+// instead (the same candidate offered twice changes no argmin).  Otherwise as
+// jfa_column_interior.
+template <int K, int NR>
+__device__ __forceinline__ void jfa_column_band(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int nx,
+                                                int64_t plane, int x, int y, int dy0, int rz, int nq, int q0, int q1,
+                                                int m20, int m10) {
+    const int m2x = -2 * x, m2y = -2 * y;
+    const int64_t step = (int64_t)K * plane;
+    const int offl = x >= K ? -K : 0, offr = x + K < nx ? K : 0;
+    const long long none = 0x7fffffffffffffffll;
+    long long a0 = none, a1 = none, a2 = none;  // outputs p-1, p, p+1
+    const uint32_t* r[NR];
+    r[0] = in + (int64_t)(rz + (q0 - 1) * K) * plane + (int64_t)(y + dy0 * K) * nx + x;
+#pragma unroll
+    for (int i = 1; i < NR; ++i) r[i] = r[i - 1] + (int64_t)K * nx;
+    for (int p = q0 - 1; p <= q1; ++p) {
+        if (p >= 0 && p < nq) {
+            const int z = rz + p * K;
+            const int m2z_prev = -2 * (z - K), m2z = -2 * z, m2z_next = -2 * (z + K);
+            uint32_t t[3 * NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                t[3 * i] = __ldg(r[i] + offl);
+                t[3 * i + 1] = __ldg(r[i]);
+                t[3 * i + 2] = __ldg(r[i] + offr);
+            }
+#pragma unroll
+            for (int i = 0; i < 3 * NR; ++i) {
+                const uint32_t s = t[i];
+                const uint32_t uz = s >> 20;
+                const uint32_t rr = uz * (uint32_t)m20 + s;
+                const uint32_t uy = rr >> 10;
+                const int sx = (int)(uy * (uint32_t)m10 + rr);
+                const int sy = (int)uy, sz = (int)uz;
+                int dxy = sx * m2x;
+                dxy = sx * sx + dxy;
+                dxy = sy * m2y + dxy;
+                dxy = sy * sy + dxy;
+                dxy = sz * sz + dxy;
+                a0 = min(a0, (long long)(((unsigned long long)(uint32_t)(dxy + m2z_prev * sz) << 32) | s));
+                a1 = min(a1, (long long)(((unsigned long long)(uint32_t)(dxy + m2z * sz) << 32) | s));
+                a2 = min(a2, (long long)(((unsigned long long)(uint32_t)(dxy + m2z_next * sz) << 32) | s));
+            }
+        }
+        const int done = p - 1;
+        if (done >= q0 && done < q1) out[(int64_t)(rz + done * K) * plane + (int64_t)y * nx + x] = (uint32_t)a0;
+        a0 = a1;
+        a1 = a2;
+        a2 = none;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) r[i] += step;
+    }
+}
+
+// Any column, any offset (the non-power-of-two ones): bounds-checked taps, empty taps skipped.
 __device__ __forceinline__ void jfa_column_generic(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                                    int nx, int ny, int64_t plane, int k, int x, int y, int rz,
                                                    int nq, int q0, int q1) {
@@ -151,14 +211,26 @@ __device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint
     const int q0 = ch * kChunk, q1 = min(nq, q0 + kChunk);
     if (x >= nx || y >= ny || q0 >= q1) return;
     const int64_t plane = (int64_t)nx * ny;
-    if (x >= k && x + k < nx && y >= k && y + k < ny) {
-        switch (k) {
-#define RTSDF_JFA_ONE(K) \
-    case K: jfa_column_interior<K>(in, out, nx, plane, x, y, rz, nq, q0, q1, m20, m10); return;
-            RTSDF_JFA_CASES(RTSDF_JFA_ONE)
+    // tap rows inside the grid (warp-uniform) and whether every lane's tap columns are
+    const bool ylo = y >= k, yhi = y + k < ny;
+    const bool xin = __all_sync(__activemask(), x >= k && x + k < nx);
+    switch (k) {
+#define RTSDF_JFA_ONE(K)                                                                                          \
+    case K:                                                                                                       \
+        if (ylo && yhi) {                                                                                         \
+            if (xin)                                                                                              \
+                jfa_column_interior<K>(in, out, nx, plane, x, y, rz, nq, q0, q1, m20, m10);                       \
+            else                                                                                                  \
+                jfa_column_band<K, 3>(in, out, nx, plane, x, y, -1, rz, nq, q0, q1, m20, m10);                    \
+        } else if (ylo || yhi) {                                                                                  \
+            jfa_column_band<K, 2>(in, out, nx, plane, x, y, ylo ? -1 : 0, rz, nq, q0, q1, m20, m10);              \
+        } else {                                                                                                  \
+            jfa_column_band<K, 1>(in, out, nx, plane, x, y, 0, rz, nq, q0, q1, m20, m10);                         \
+        }                                                                                                         \
+        return;
+        RTSDF_JFA_CASES(RTSDF_JFA_ONE)
 #undef RTSDF_JFA_ONE
-            default: break;
-        }
+        default: break;
     }
     jfa_column_generic(in, out, nx, ny, plane, k, x, y, rz, nq, q0, q1);
 }
