@@ -1,4 +1,6 @@
-// 3D jump flooding (Sec. 2.2): one launch per offset k, Jacobi ping-pong.
+// 3D jump flooding (Sec. 2.2): one launch per offset k, Jacobi ping-pong.  Offsets
+// 64..256 whose residue classes hold at most kGroupMaxPlanes planes run the grouped
+// kernel (several classes per thread); the others one class chunk per thread.
 #include "jfa_core.cuh"
 #include "rtsdf_launch.cuh"
 
@@ -10,6 +12,13 @@ __global__ void __launch_bounds__(kJX* kJY) k_jfa_pass(const uint32_t* __restric
     jfa_column(in, out, nx, ny, nz, k, nchunk, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
 }
 
+template <int K>
+__global__ void __launch_bounds__(kJX* kJY) k_jfa_pass_grouped(const uint32_t* __restrict__ in,
+                                                             uint32_t* __restrict__ out, int nx, int ny, int nz,
+                                                             int grp, int m20, int m10) {
+    jfa_column_grouped<K>(in, out, nx, ny, nz, grp, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
+}
+
 rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* steps, int32_t nsteps,
                  int32_t** result, cudaStream_t s) {
     uint32_t* src = reinterpret_cast<uint32_t*>(a);
@@ -19,8 +28,21 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
         const int k = steps[i];
         const int nq = (g.nz + k - 1) / k;
         const int nchunk = (nq + kChunk - 1) / kChunk;
-        const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)(k * nchunk));
-        k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, -(1 << 20), -(1 << 10));
+        const bool pow2 = k >= 64 && k <= 256 && (k & (k - 1)) == 0;
+        if (pow2 && nq <= kGroupMaxPlanes) {
+            const int grp = kChunk / nq;
+            const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)((k + grp - 1) / grp));
+            const int m20 = -(1 << 20), m10 = -(1 << 10);
+            if (k == 64)
+                k_jfa_pass_grouped<64><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
+            else if (k == 128)
+                k_jfa_pass_grouped<128><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
+            else
+                k_jfa_pass_grouped<256><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
+        } else {
+            const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)(k * nchunk));
+            k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, -(1 << 20), -(1 << 10));
+        }
         RTSDF_LAUNCHED();
         uint32_t* t = src; src = dst; dst = t;
     }

@@ -30,6 +30,7 @@ __device__ __forceinline__ void offer(Best& b, int d, uint32_t s) {
 
 constexpr int kJX = 32, kJY = 8;  // block of columns (x, y)
 constexpr int kChunk = 16;        // outputs per column and block along z
+constexpr int kGroupMaxPlanes = kChunk / 2;  // classes this short are grouped per thread
 
 // One thread per (x, y) column and z-chunk of one residue class mod k: the planes
 // z = rz + p*k stream past; each loaded tap is decoded once and offered to the
@@ -233,6 +234,43 @@ __device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint
         default: break;
     }
     jfa_column_generic(in, out, nx, ny, plane, k, x, y, rz, nq, q0, q1);
+}
+
+// Large offsets (every residue class holds at most kGroupMaxPlanes planes): one
+// thread takes grp consecutive classes of its column, so its fixed costs are spread
+// over about kChunk outputs.  Its own kernel, so the loop does not weigh on the
+// register allocation of the common path.
+template <int K>
+__device__ __forceinline__ void jfa_column_grouped_k(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                     int nx, int ny, int nz, int64_t plane, int x, int y, int rz0,
+                                                     int grp, bool xin, int m20, int m10) {
+    const bool ylo = y >= K, yhi = y + K < ny;
+    for (int c = 0; c < grp; ++c) {
+        const int rz = rz0 + c;
+        if (rz >= K || rz >= nz) break;
+        const int nq = (nz - rz + K - 1) / K;
+        if (ylo && yhi) {
+            if (xin)
+                jfa_column_interior<K>(in, out, nx, plane, x, y, rz, nq, 0, nq, m20, m10);
+            else
+                jfa_column_band<K, 3>(in, out, nx, plane, x, y, -1, rz, nq, 0, nq, m20, m10);
+        } else if (ylo || yhi) {
+            jfa_column_band<K, 2>(in, out, nx, plane, x, y, ylo ? -1 : 0, rz, nq, 0, nq, m20, m10);
+        } else {
+            jfa_column_band<K, 1>(in, out, nx, plane, x, y, 0, rz, nq, 0, nq, m20, m10);
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void jfa_column_grouped(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                   int nx, int ny, int nz, int grp, int bx, int by, int bz, int m20,
+                                                   int m10) {
+    const int x = bx * kJX + threadIdx.x;
+    const int y = by * kJY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const bool xin = __all_sync(__activemask(), x >= K && x + K < nx);
+    jfa_column_grouped_k<K>(in, out, nx, ny, nz, (int64_t)nx * ny, x, y, bz * grp, grp, xin, m20, m10);
 }
 
 }  // namespace rtsdf
