@@ -602,7 +602,7 @@ def run_ours(args):
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the ten passes of one
     # room frame, from one ncu capture of this kernel version
     traffic = JFA_ROOM_DRAM_BYTES_PER_FRAME if args.workload == "room" else None
-    roofline = {"kernel": "k_jfa_pass (all passes of a frame)", "bound": "hbm", "achieved": round(jfa_gbs, 1),
+    roofline = {"kernel": "k_jfa_pass + k_jfa_pass_grouped (all passes of a frame)", "bound": "hbm", "achieved": round(jfa_gbs, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(jfa_gbs / hbm_peak, 4), "traffic": traffic,
                 "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes,
                 "limit": "integer ALU and FMA-heavy pipes (half-rate), not HBM"}
