@@ -111,8 +111,29 @@ __device__ __forceinline__ void bvh_leaf_up(const float* __restrict__ verts, int
     leaves[j].e1 = make_float4(e1.x, e1.y, e1.z, 0.0f);
     leaves[j].e2 = make_float4(e2.x, e2.y, e2.z, 0.0f);
     {
-        const float3 cen = make_float3((a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
-                                       (a.z + b.z + c.z) * (1.0f / 3.0f));
+        // centre of the smallest sphere around the triangle: the midpoint of the side
+        // opposite an obtuse (or right) angle, else the circumcentre; the radius is then
+        // measured to the three vertices, so the sphere holds them whatever the rounding
+        const float3 ab = sub3(b, a), ac = sub3(c, a), bc = sub3(c, b);
+        const float3 w = cross3(ab, ac);
+        const float w2 = dot3(w, w);
+        float3 cen;
+        if (dot3(ab, ac) <= 0.0f) {
+            cen = make_float3(0.5f * (b.x + c.x), 0.5f * (b.y + c.y), 0.5f * (b.z + c.z));
+        } else if (-dot3(ab, bc) <= 0.0f) {
+            cen = make_float3(0.5f * (a.x + c.x), 0.5f * (a.y + c.y), 0.5f * (a.z + c.z));
+        } else if (dot3(ac, bc) <= 0.0f) {
+            cen = make_float3(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z));
+        } else if (w2 > 0.0f) {
+            const float sab = dot3(ab, ab), sac = dot3(ac, ac);
+            const float3 p = cross3(ac, w), q = cross3(w, ab);
+            const float inv = 0.5f / w2;
+            cen = make_float3(a.x + (sab * p.x + sac * q.x) * inv, a.y + (sab * p.y + sac * q.y) * inv,
+                              a.z + (sab * p.z + sac * q.z) * inv);
+        } else {
+            cen = make_float3((a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
+                              (a.z + b.z + c.z) * (1.0f / 3.0f));
+        }
         const float3 da = sub3(a, cen), db = sub3(b, cen), dc = sub3(c, cen);
         const float r = sqrtf(fmaxf(fmaxf(dot3(da, da), dot3(db, db)), dot3(dc, dc)));
         // margin far above the FP32 rounding of any accepted hit point

@@ -236,7 +236,7 @@ struct alignas(16) BvhLeaf {
     float4 v0;   // xyz = vertex A (voxel space), w = triangle id (int bits)
     float4 e1;   // B - A
     float4 e2;   // C - A
-    float4 sph;  // bounding sphere: centroid xyz, w = radius + margin (a superset of the triangle)
+    float4 sph;  // smallest enclosing sphere: centre xyz, w = radius + margin (a superset of the triangle)
     float4 pln;  // unit normal xyz (0 for a degenerate triangle), w = normal . A
 };
 
