@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ Bat
 }
 
 template <int BX, int BY, int BZ, int RPL>
-__global__ void __launch_bounds__(kRefineMaxThreads, kRefineWarpsPerSm * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t, BatchGrids G,
+__global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t, BatchGrids G,
                                                                   uint32_t frame, int accumulate,
                                                                   const char* __restrict__ bvh,
                                                                   const unsigned long long* __restrict__ bmask,
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kRefineMaxThreads, kRefineWarpsPerSm * 32 / kR
                                                                   rtsdf_counters* counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+    WarpSmemT<RPL>& w = reinterpret_cast<WarpSmemT<RPL>*>(smem_raw)[warp];
     const uint32_t nact = count[0];
     uint32_t n_hit = 0, n_fail = 0, n_ovf = 0;
     while (true) {
@@ -532,17 +532,17 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     RTSDF_CUDA(cudaMemsetAsync(count, 0, 16, s));
     k_bresolve<BX, BY, BZ><<<P.ntiles, 512, 0, s>>>(t, G, frame, accumulate, bmask, blist, count);
     RTSDF_LAUNCHED();
-    const size_t smem = sizeof(WarpSmem) * (size_t)warps;
+    const size_t smem = sizeof(WarpSmemT<RPL>) * (size_t)warps;
     static bool attr_set[64] = {false};
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(WarpSmem) * 4)));
+                                        (int)(sizeof(WarpSmemT<RPL>) * 4)));
         attr_set[dev] = true;
     }
     // the same resident warps per SM for every CTA size (shared memory bound)
-    k_brefine<BX, BY, BZ, RPL><<<num_sms() * (kRefineWarpsPerSm / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
+    k_brefine<BX, BY, BZ, RPL><<<num_sms() * (refine_warps_per_sm<RPL>() / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
                                                                             static_cast<const char*>(B.bvh), bmask,
                                                                             blist, count, counters);
     RTSDF_LAUNCHED();
@@ -560,12 +560,15 @@ rtsdf_status refine_step(const rtsdf_batch_plan& P, const rtsdf_batch_buffers& B
     const int w = tu.warps_per_cta;
     int rmax = 1;  // one ray group per brick for up to rpl rays (the largest ray count of the batch)
     for (const rtsdf_batch_scene& sc : P.scenes) rmax = sc.refine.rays_per_voxel > rmax ? sc.refine.rays_per_voxel : rmax;
-    const int rpl = rmax <= 2 ? 2 : (rmax <= 4 ? 4 : 8);
+    const int rpl = rmax <= 2 ? 2 : (rmax <= 4 ? 4 : (rmax <= 8 ? 8 : 16));
 #define RTSDF_BATCH_CASE(X, Y, Z, R) \
     if (tu.brick_x == X && rpl == R) return launch_refine<X, Y, Z, R>(P, B, frame, accumulate, counters, w, s);
     RTSDF_BATCH_CASE(4, 4, 4, 2) RTSDF_BATCH_CASE(4, 4, 4, 4) RTSDF_BATCH_CASE(4, 4, 4, 8)
+    RTSDF_BATCH_CASE(4, 4, 4, 16)
     RTSDF_BATCH_CASE(8, 4, 2, 2) RTSDF_BATCH_CASE(8, 4, 2, 4) RTSDF_BATCH_CASE(8, 4, 2, 8)
+    RTSDF_BATCH_CASE(8, 4, 2, 16)
     RTSDF_BATCH_CASE(16, 2, 2, 2) RTSDF_BATCH_CASE(16, 2, 2, 4) RTSDF_BATCH_CASE(16, 2, 2, 8)
+    RTSDF_BATCH_CASE(16, 2, 2, 16)
 #undef RTSDF_BATCH_CASE
     return RTSDF_EINVAL;
 }

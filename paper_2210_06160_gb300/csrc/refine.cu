@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(512, 4) k_resolve(RefineArgs a, const int32_t*
 
 // Persistent: warps take bricks from the work list until it is exhausted.
 template <bool kTrack, int RPL>
-__global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefineThreads) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 32 / kRefineThreads) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
                                                               const int32_t* __restrict__ nearest,
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefi
                                                               int32_t* __restrict__ win_tri) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+    WarpSmemT<RPL>& w = reinterpret_cast<WarpSmemT<RPL>*>(smem_raw)[warp];
     const int n_leaves = hdr->n_leaves;
     const int n_inner = n_leaves > 1 ? n_leaves - 1 : 1;
     const uint32_t nact = count[0];
@@ -118,11 +118,12 @@ __global__ void __launch_bounds__(kRefineThreads, kRefineWarpsPerSm * 32 / kRefi
 }
 
 template <bool kTrack, int RPL>
-static rtsdf_status launch_refine_t(size_t smem, cudaStream_t s, const RefineArgs& a, const BvhHeader* hdr,
+static rtsdf_status launch_refine_t(cudaStream_t s, const RefineArgs& a, const BvhHeader* hdr,
                                     const BvhNode* nodes, const BvhLeaf* leaves, const int32_t* nearest,
                                     const int32_t* rep_tri, const unsigned long long* bmask, const int32_t* blist,
                                     uint32_t* count, uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
                                     rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
+    const size_t smem = sizeof(WarpSmemT<RPL>) * (kRefineThreads / 32);
     static bool attr_set[64] = {};
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
@@ -130,13 +131,13 @@ static rtsdf_status launch_refine_t(size_t smem, cudaStream_t s, const RefineArg
         RTSDF_CUDA(cudaFuncSetAttribute(k_refine<kTrack, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set[dev] = true;
     }
-    k_refine<kTrack, RPL><<<num_sms() * (kRefineWarpsPerSm * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
+    k_refine<kTrack, RPL><<<num_sms() * (refine_warps_per_sm<RPL>() * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
         a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count, dist_bits, front, back, sdf, counters, win_ray,
         win_tri);
     return RTSDF_OK;
 }
 
-static rtsdf_status launch_refine_kernel(bool track, int rpl, size_t smem, cudaStream_t s, const RefineArgs& a,
+static rtsdf_status launch_refine_kernel(bool track, int rpl, cudaStream_t s, const RefineArgs& a,
                                          const BvhHeader* hdr, const BvhNode* nodes, const BvhLeaf* leaves,
                                          const int32_t* nearest, const int32_t* rep_tri,
                                          const unsigned long long* bmask, const int32_t* blist, uint32_t* count,
@@ -144,11 +145,11 @@ static rtsdf_status launch_refine_kernel(bool track, int rpl, size_t smem, cudaS
                                          rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
 #define RTSDF_REFINE_CASE(T, R)                                                                                 \
     if (track == T && rpl == R)                                                                                 \
-        return launch_refine_t<T, R>(smem, s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count,     \
+        return launch_refine_t<T, R>(s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count,           \
                                      dist_bits, front, back, sdf, counters, T ? win_ray : nullptr,              \
                                      T ? win_tri : nullptr);
-    RTSDF_REFINE_CASE(false, 2) RTSDF_REFINE_CASE(false, 4) RTSDF_REFINE_CASE(false, 8)
-    RTSDF_REFINE_CASE(true, 2) RTSDF_REFINE_CASE(true, 4) RTSDF_REFINE_CASE(true, 8)
+    RTSDF_REFINE_CASE(false, 2) RTSDF_REFINE_CASE(false, 4) RTSDF_REFINE_CASE(false, 8) RTSDF_REFINE_CASE(false, 16)
+    RTSDF_REFINE_CASE(true, 2) RTSDF_REFINE_CASE(true, 4) RTSDF_REFINE_CASE(true, 8) RTSDF_REFINE_CASE(true, 16)
 #undef RTSDF_REFINE_CASE
     return RTSDF_EINVAL;
 }
@@ -203,9 +204,8 @@ rtsdf_status refine(const rtsdf_grid& gh, int32_t T, const void* bvh, const int3
     k_resolve<<<rgrid, 512, 0, s>>>(a, nearest, rep_tri, dist_bits, front, back, sdf, w.bmask, w.blist, w.count,
                                     track ? win_ray : nullptr, track ? win_tri : nullptr);
     RTSDF_LAUNCHED();
-    const size_t smem = sizeof(WarpSmem) * (kRefineThreads / 32);
-    const int rpl = a.R <= 2 ? 2 : (a.R <= 4 ? 4 : 8);  // one ray group for up to rpl rays
-    RTSDF_TRY(launch_refine_kernel(track, rpl, smem, s, a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
+    const int rpl = a.R <= 2 ? 2 : (a.R <= 4 ? 4 : (a.R <= 8 ? 8 : 16));  // one ray group for up to rpl rays
+    RTSDF_TRY(launch_refine_kernel(track, rpl, s, a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
                                    w.count, dist_bits, front, back, sdf, counters, win_ray, win_tri));
     RTSDF_LAUNCHED();
     if (counters) {

@@ -14,10 +14,10 @@ namespace rtsdf {
 constexpr int kListCap = 256;        // staged leaves per warp and round
 constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
 constexpr int kNarrowMargin = 96;    // > depth of any tree the builder makes (30-bit codes + 32 index bits)
-constexpr int kRaysPerLane = 8;      // most rays of a voxel per group (one lane per voxel)
-constexpr int kQueueCap = 32 + 32 * kRaysPerLane;    // queued ray/triangle items per warp (< 32 + one round)
+constexpr int kRaysPerLane = 8;      // rays of a voxel per group for up to 8 rays (one lane per voxel)
 constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
 constexpr int kRefineWarpsPerSm = 20;                 // resident refine warps per SM (shared memory bound)
+constexpr int kRefineWarpsPerSm16 = 12;               // the same with 16-ray groups (twice the ray rows)
 
 template <int BX, int BY, int BZ>
 struct BrickShape {
@@ -228,31 +228,51 @@ __device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes,
     return nc;
 }
 
+// Sizes of the per-warp state for RPL rays per lane and group: groups of up to 8 rays
+// share one layout; 16-ray groups (9 to 16 rays per voxel) have twice the ray rows.
+template <int RPL>
+struct RaySlots {
+    static constexpr int kRays = RPL <= 8 ? 8 : RPL;  // ray rows of the direction and closest-hit arrays
+    static constexpr int kQuads = kRays / 4;
+    static constexpr int kRBits = RPL <= 8 ? 3 : 4;   // ray bits of a queued item
+    static constexpr int kQueue = 32 + 32 * kRays;    // < 32 left over + one filter round
+};
+
+// Resident refine warps per SM for RPL rays per lane and group.
+template <int RPL>
+constexpr int refine_warps_per_sm() {
+    return RPL <= 8 ? kRefineWarpsPerSm : kRefineWarpsPerSm16;
+}
+
 // Per-warp shared state of k_refine.
-struct WarpSmem {
-    int list[kListCap];             // staged leaves
+template <int RPL>
+struct WarpSmemT {
+    int list[kListCap];                          // staged leaves
     int stack[kStackCapW];
-    uint32_t queue[kQueueCap];      // (list index << 8) | (slot << 3) | ray
-    int qn;                         // queued items
-    uint32_t okm[32];               // rays of each slot that drew a direction
-    float4 origin[32];              // voxel centres of the pass's slots
-    float4 dq[3][2][32];            // ray directions: [component][ray / 4][slot], rays 4q..4q+3 in x..w
-    float4 tsph[32];                // bounding spheres of the chunk's staged triangles
-    float4 tpln[32];                // their planes
-    uint16_t pairs[160];            // (slot << 5) | chunk lane: (voxel, triangle) pairs to filter
-    unsigned long long key[8][32];  // closest hit: (t bits << 32) | (id << 1) | front
+    uint32_t queue[RaySlots<RPL>::kQueue];        // (list index << (5 + rbits)) | (slot << rbits) | ray
+    int qn;                                      // queued items
+    uint32_t okm[32];                            // rays of each slot that drew a direction
+    float4 origin[32];                           // voxel centres of the pass's slots
+    float4 dq[3][RaySlots<RPL>::kQuads][32];      // ray directions: [component][ray / 4][slot], rays 4q..4q+3 in x..w
+    float4 tsph[32];                             // bounding spheres of the chunk's staged triangles
+    float4 tpln[32];                             // their planes
+    uint16_t pairs[160];                         // (slot << 5) | chunk lane: (voxel, triangle) pairs to filter
+    unsigned long long key[RaySlots<RPL>::kRays][32];  // closest hit: (t bits << 32) | (id << 1) | front
 };
 
 // Component comp of ray r's direction at a slot (one scalar shared-memory load).
-__device__ __forceinline__ float dq_comp(const WarpSmem& w, int comp, int r, int slot) {
+template <int RPL>
+__device__ __forceinline__ float dq_comp(const WarpSmemT<RPL>& w, int comp, int r, int slot) {
     return reinterpret_cast<const float*>(&w.dq[comp][r >> 2][slot])[r & 3];
 }
 
 // Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
 // closest hit per ray (ties to the lower id) is kept with a 64-bit atomicMin.
-__device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
+template <int RPL>
+__device__ __forceinline__ void run_item(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
                                          float tmax) {
-    const int c = (int)(item >> 8), slot = (int)((item >> 3) & 31u), r = (int)(item & 7u);
+    constexpr int kB = RaySlots<RPL>::kRBits;
+    const int c = (int)(item >> (5 + kB)), slot = (int)((item >> kB) & 31u), r = (int)(item & ((1u << kB) - 1u));
     const float4 of = w.origin[slot];
     const float3 o = make_float3(of.x, of.y, of.z),
                  d = make_float3(dq_comp(w, 0, r, slot), dq_comp(w, 1, r, slot), dq_comp(w, 2, r, slot));
@@ -279,7 +299,7 @@ __device__ __forceinline__ void run_item(WarpSmem& w, const BvhLeaf* __restrict_
 // widened by eps in sd.  All margins exceed the FP32 rounding of both sides, so no
 // triangle the exact test accepts is dropped.
 template <int RPL>
-__device__ __forceinline__ uint32_t filter_pair(const WarpSmem& w, int v, int j, float tmax) {
+__device__ __forceinline__ uint32_t filter_pair(const WarpSmemT<RPL>& w, int v, int j, float tmax) {
     const float4 o = w.origin[v];
     const float4 sph = w.tsph[j], pl = w.tpln[j];
     const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
@@ -318,7 +338,8 @@ __device__ __forceinline__ uint32_t filter_pair(const WarpSmem& w, int v, int j,
 }
 
 // Exact tests of full batches of 32 queued items.
-__device__ __forceinline__ void run_full_batches(WarpSmem& w, const BvhLeaf* __restrict__ leaves, float tmax) {
+template <int RPL>
+__device__ __forceinline__ void run_full_batches(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, float tmax) {
     const int lane = threadIdx.x & 31;
     int qn = w.qn;
     if (qn >= 32) {
@@ -335,7 +356,7 @@ __device__ __forceinline__ void run_full_batches(WarpSmem& w, const BvhLeaf* __r
 // Filters one (voxel slot, chunk triangle) pair per lane (lanes >= n idle) and queues
 // the surviving (voxel, ray, triangle) items.
 template <int RPL>
-__device__ __forceinline__ void filter_and_queue(WarpSmem& w, int n, int base, int cb, float tmax) {
+__device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int base, int cb, float tmax) {
     const int lane = threadIdx.x & 31;
     if (lane < n) {
         const uint32_t p = w.pairs[base + lane];
@@ -346,7 +367,8 @@ __device__ __forceinline__ void filter_and_queue(WarpSmem& w, int n, int base, i
             while (pm) {
                 const int r = __ffs(pm) - 1;
                 pm &= pm - 1u;
-                w.queue[pos++] = ((uint32_t)(cb + j) << 8) | ((uint32_t)v << 3) | (uint32_t)r;
+                w.queue[pos++] = ((uint32_t)(cb + j) << (5 + RaySlots<RPL>::kRBits)) |
+                                 ((uint32_t)v << RaySlots<RPL>::kRBits) | (uint32_t)r;
             }
         }
     }
@@ -377,7 +399,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                                              int by, int bz, uint32_t* __restrict__ dist_bits,
                                              uint32_t* __restrict__ front, uint32_t* __restrict__ back,
                                              float* __restrict__ sdf, uint32_t* __restrict__ win_ray,
-                                             int32_t* __restrict__ win_tri, WarpSmem& w, uint32_t& n_hit,
+                                             int32_t* __restrict__ win_tri, WarpSmemT<RPL>& w, uint32_t& n_hit,
                                              uint32_t& n_fail, uint32_t& n_ovf) {
     const int lane = threadIdx.x & 31;
     const float ext = a.tmax * 1.00001f + 1e-3f;
