@@ -121,3 +121,25 @@ def test_48_scene_batch_matches_single_scene_builds():
         assert m.sum() > 0
         _assert_same(got, plain, m, sc.name)
         torch.cuda.empty_cache()
+
+
+def test_batch_at_capacity_matches_single_scene_builds():
+    """RTSDF_BATCH_MAX_SCENES (64) small scenes of ragged sizes in one plan (full scene and
+    JFA pass tables): every scene bit-identical to its own single-scene build."""
+    scs = []
+    seed = 100
+    while len(scs) < 64:
+        for sc in scenes.scene_batch_small(seed=seed):
+            if len(scs) < 64:
+                scs.append(dataclasses.replace(sc, refine=dataclasses.replace(sc.refine, scene_id=len(scs))))
+        seed += 1
+    B = rt.Batch(scs)
+    B.rebuild(0, False)
+    torch.cuda.synchronize()
+    c = rt.counters_dict(B.counters)
+    assert c["rays_failed"] == 0 and c["stack_overflow"] == 0
+    for i, sc in enumerate(scs):
+        got = _batch_scene_arrays(B, i)
+        plain = _plain(sc)
+        m = _mask_from_nearest(sc.grid, plain["nearest"], sc.refine.mask_vox)
+        _assert_same(got, plain, m, f"{sc.name} #{i}")
