@@ -75,6 +75,19 @@ def test_random_triangles_ragged_grid_parity(R):
     assert got["counters"]["skipped_triangles"] == 2 * 2  # voxelize + BVH each count both
 
 
+def test_sign_fallback_off_parity():
+    """sign_fallback = 0: voxels whose front and back votes tie (including no hit) take +dist
+    instead of the representative plane's side; whole grids against the oracle."""
+    sc = scenes.scene_small_room(seed=9, n=30)
+    sc = dataclasses.replace(sc, refine=dataclasses.replace(sc.refine, sign_fallback=False))
+    ref = oracle.rebuild(sc)
+    got, _ = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+    m = ref["mask"].astype(bool)
+    tie = m & (ref["front"] == ref["back"])
+    assert tie.sum() > 0 and np.all(got["sdf"][tie] >= 0.0)
+
+
 def _dense_cluster_scene(R: int, n: int = 3000):
     """n small triangles packed in a ball of radius 2.5 voxels: every brick near it
     reaches far more triangles than one staging round of the refine walk holds."""
