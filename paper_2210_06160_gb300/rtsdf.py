@@ -553,8 +553,9 @@ def rtsdf_batch_plan_create(scenes: list) -> C.c_void_p:
     return plan
 
 
-def rtsdf_batch_rebuild(plan, buffers: BatchBuffers, frame_index: int, accumulate: bool, counters=None,
+def rtsdf_batch_rebuild(plan, buffers: BatchBuffers, frame_index: int, accumulate: int, counters=None,
                         stream=None) -> None:
+    """accumulate: 0 fresh, 1 (or True) minimum over frames, 2 the Eq. (1) decay with each scene's alpha."""
     _check(lib().rtsdf_batch_rebuild(plan, C.byref(buffers), int(frame_index) & 0xFFFFFFFF, int(accumulate),
                                      _dev(counters, torch.int32, "counters"), _stream(stream)), "rtsdf_batch_rebuild")
 
@@ -610,7 +611,7 @@ class Batch:
                                     self.bvh.numel(), self.dist_bits.data_ptr(), self.front.data_ptr(),
                                     self.back.data_ptr(), self.sdf.data_ptr(), self.ws.data_ptr(), self.ws.numel())
 
-    def rebuild(self, frame_index: int = 0, accumulate: bool = False, stream=None):
+    def rebuild(self, frame_index: int = 0, accumulate: int = 0, stream=None):
         rtsdf_batch_rebuild(self.plan, self.buffers, frame_index, accumulate, self.counters, stream)
 
     def autotune(self, reps: int = 3, stream=None) -> float:

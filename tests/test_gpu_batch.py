@@ -143,3 +143,19 @@ def test_batch_at_capacity_matches_single_scene_builds():
         plain = _plain(sc)
         m = _mask_from_nearest(sc.grid, plain["nearest"], sc.refine.mask_vox)
         _assert_same(got, plain, m, f"{sc.name} #{i}")
+
+
+def test_batch_decay_matches_single_scene_builds():
+    """accumulate = 2 (the Eq. (1) decay with each scene's alpha) in one batch: frame 0 fresh,
+    frames 1 and 2 decayed; every scene bit-identical to its own single-scene sequence."""
+    scs = [dataclasses.replace(sc, refine=dataclasses.replace(sc.refine, accumulate=2, decay_alpha=0.9))
+           for sc in scenes.scene_batch_small()]
+    B = rt.Batch(scs)
+    for f in range(3):
+        B.rebuild(f, 2 if f > 0 else 0)
+    torch.cuda.synchronize()
+    for i, sc in enumerate(scs):
+        plain = _plain(sc, frames=3)
+        got = _batch_scene_arrays(B, i)
+        m = _mask_from_nearest(sc.grid, plain["nearest"], sc.refine.mask_vox)
+        _assert_same(got, plain, m, sc.name + " decay")
