@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SDF rebuild ms/frame @400x200x400, GVoxel/s, %HBM roof; bwd+batch vs plain"
-JFA_ROOM_DRAM_BYTES_PER_FRAME = 2_207_083_264
+JFA_ROOM_DRAM_BYTES_PER_FRAME = 2_209_870_592
 # smsp__inst_executed.sum of k_refine for one room frame (8 rays, 7.24 M masked voxels), from one
 # ncu capture of this kernel version; the refine kernel is bound by instruction issue, not bytes
 REFINE_ROOM_WARP_INSTR_PER_FRAME = 3_805_157_363

@@ -28,8 +28,8 @@ __device__ __forceinline__ void offer(Best& b, int d, uint32_t s) {
     }
 }
 
-constexpr int kJX = 32, kJY = 8;  // block of columns (x, y)
-constexpr int kChunk = 16;        // outputs per column and block along z
+constexpr int kJX = 32, kJY = 4;  // block of columns (x, y)
+constexpr int kChunk = 32;        // outputs per column and block along z
 constexpr int kGroupMaxPlanes = kChunk / 2;  // classes this short are grouped per thread
 
 // One thread per (x, y) column and z-chunk of one residue class mod k: the planes
