@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kJX* kJY) k_bjfa_pass(const __grid_constant__ 
     }
     const PassD& e = p.e[lo];
     const int local = b - e.block_start;
-    jfa_column(e.in, e.out, e.nx, e.ny, e.nz, e.k, e.nchunk, local % e.gbx, (local / e.gbx) % e.gby,
+    jfa_column(e.in, e.out, e.nx, e.ny, e.nz, e.k, e.nchunk, kChunk, local % e.gbx, (local / e.gbx) % e.gby,
                local / (e.gbx * e.gby), p.m20, p.m10);
 }
 

@@ -8,8 +8,9 @@ namespace rtsdf {
 
 // m20 = -2^20 and m10 = -2^10 (see jfa_column_interior)
 __global__ void __launch_bounds__(kJX* kJY) k_jfa_pass(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                     int nx, int ny, int nz, int k, int nchunk, int m20, int m10) {
-    jfa_column(in, out, nx, ny, nz, k, nchunk, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
+                                                     int nx, int ny, int nz, int k, int nchunk, int chunk, int m20,
+                                                     int m10) {
+    jfa_column(in, out, nx, ny, nz, k, nchunk, chunk, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
 }
 
 template <int K>
@@ -24,10 +25,11 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
     uint32_t* src = reinterpret_cast<uint32_t*>(a);
     uint32_t* dst = reinterpret_cast<uint32_t*>(b);
     const dim3 block(kJX, kJY, 1);
+    const int chunk = (int64_t)g.nx * g.ny * g.nz >= (int64_t)(16 << 20) ? kChunk : kChunkSmall;
     for (int i = 0; i < nsteps; ++i) {
         const int k = steps[i];
         const int nq = (g.nz + k - 1) / k;
-        const int nchunk = (nq + kChunk - 1) / kChunk;
+        const int nchunk = (nq + chunk - 1) / chunk;
         const bool pow2 = k >= 64 && k <= 256 && (k & (k - 1)) == 0;
         if (pow2 && nq <= kGroupMaxPlanes) {
             const int grp = kChunk / nq;
@@ -41,7 +43,8 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
                 k_jfa_pass_grouped<256><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
         } else {
             const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)(k * nchunk));
-            k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, -(1 << 20), -(1 << 10));
+            k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, chunk, -(1 << 20),
+                                              -(1 << 10));
         }
         RTSDF_LAUNCHED();
         uint32_t* t = src; src = dst; dst = t;

@@ -29,7 +29,8 @@ __device__ __forceinline__ void offer(Best& b, int d, uint32_t s) {
 }
 
 constexpr int kJX = 32, kJY = 4;  // block of columns (x, y)
-constexpr int kChunk = 32;        // outputs per column and block along z
+constexpr int kChunk = 32;        // outputs per column and block along z (grids of 16 M voxels and more)
+constexpr int kChunkSmall = 16;   // the same for smaller grids, which need more threads to fill the GPU
 constexpr int kGroupMaxPlanes = kChunk / 2;  // classes this short are grouped per thread
 
 // One thread per (x, y) column and z-chunk of one residue class mod k: the planes
@@ -204,12 +205,13 @@ __device__ __forceinline__ void jfa_column_generic(const uint32_t* __restrict__ 
 
 // One thread: output column (x, y) over a block of z-planes of one residue class mod k.
 __device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int nx, int ny,
-                                           int nz, int k, int nchunk, int bx, int by, int bz, int m20, int m10) {
+                                           int nz, int k, int nchunk, int chunk, int bx, int by, int bz, int m20,
+                                           int m10) {
     const int x = bx * kJX + threadIdx.x;
     const int y = by * kJY + threadIdx.y;
     const int rz = bz / nchunk, ch = bz - rz * nchunk;
     const int nq = (nz - rz + k - 1) / k;  // planes of this residue class
-    const int q0 = ch * kChunk, q1 = min(nq, q0 + kChunk);
+    const int q0 = ch * chunk, q1 = min(nq, q0 + chunk);
     if (x >= nx || y >= ny || q0 >= q1) return;
     const int64_t plane = (int64_t)nx * ny;
     // tap rows inside the grid (warp-uniform) and whether every lane's tap columns are
