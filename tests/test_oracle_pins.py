@@ -718,3 +718,121 @@ def test_shadow_sphere_umbra_and_lit_regions(orc):
     vis = orc.shadow(g, f, pos, nrm, sp)
     assert vis[0] == 0.0 and vis[-1] == 1.0
     assert np.all(np.diff(vis) >= -1e-6)
+
+
+def _small_sphere_state(orc):
+    V, T = scenes.icosphere(2)
+    V = (V * 6.0 + 12.0).astype(np.float32)
+    g = scenes.Grid(24, 24, 24, (0.0, 0.0, 0.0), 1.0)
+    seed, rep, _ = orc.voxelize(V, T, g)
+    near = orc.jfa(g, seed, scenes.jfa_steps(g))
+    u_c, mask = orc.resolve(g, V, T, near, rep, 2.0)
+    return V, T, g, u_c, mask
+
+
+def test_accumulation_equals_independent_frames(orc):
+    """Sec. 2.1 accumulation (accumulate = 1): later frames lower the distance when
+    they find a smaller one and add their votes.  The rays of frame f depend only on
+    (voxel, f), so F accumulated frames must equal F independent fresh frames
+    combined: front and back are the sums, the distance is the minimum, and the
+    winner record is that of the earliest frame attaining it.  When the coarse
+    distance drops between frames (a moved surface), the carried distance is first
+    lowered to the new coarse value, which then takes the record back."""
+    V, T, g, u_c, mask = _small_sphere_state(orc)
+    m = mask.astype(bool).ravel()
+    vox = np.flatnonzero(m).astype(np.int32)
+    rp = scenes.RefineParams(rays_per_voxel=6, max_ray_vox=8.0, key=(11, 12), accumulate=1)
+    F = 4
+
+    def fresh(frame, uc):
+        d, fr, bk, wr, wt = (a.ravel().copy() for a in orc.init_refine_state(uc, mask))
+        orc.refine_voxels(g, V, T, vox, rp, frame, d, fr, bk, wr, wt)
+        return d.view(np.float32), fr, bk, wr, wt
+
+    state = None
+    for f in range(F):
+        state = orc.init_refine_state(u_c, mask, state, accumulate=1)
+        d, fr, bk, wr, wt = (a.ravel().copy() for a in state)
+        orc.refine_voxels(g, V, T, vox, rp, f, d, fr, bk, wr, wt)
+        state = tuple(a.reshape(g.shape_zyx) for a in (d, fr, bk, wr, wt))
+    runs = [fresh(f, u_c) for f in range(F)]
+    acc_d = state[0].ravel().view(np.float32)
+    dmin = np.min(np.stack([r[0] for r in runs]), axis=0)
+    np.testing.assert_array_equal(acc_d[m], dmin[m])
+    np.testing.assert_array_equal(acc_d[~m], u_c.ravel()[~m])
+    np.testing.assert_array_equal(state[1].ravel(), sum(r[1].astype(np.int64) for r in runs).astype(np.uint32))
+    np.testing.assert_array_equal(state[2].ravel(), sum(r[2].astype(np.int64) for r in runs).astype(np.uint32))
+    assert (state[1].ravel()[~m] == 0).all() and (state[2].ravel()[~m] == 0).all()
+    # winner record: the earliest frame whose distance equals the minimum
+    first = np.argmax(np.stack([r[0] == dmin for r in runs]), axis=0)
+    want_ray = np.choose(first, [r[3] for r in runs])
+    want_tri = np.choose(first, [r[4] for r in runs])
+    np.testing.assert_array_equal(state[3].ravel()[m], want_ray[m])
+    np.testing.assert_array_equal(state[4].ravel()[m], want_tri[m])
+    assert (state[4].ravel()[m] >= 0).sum() > 100     # most masked voxels keep a ray hit
+    # the coarse distance drops to 0.4 of its value at frame F
+    u2 = (u_c * np.float32(0.4)).astype(np.float32)
+    st = orc.init_refine_state(u2, mask, state, accumulate=1)
+    d, fr, bk, wr, wt = (a.ravel().copy() for a in st)
+    carried = np.minimum(acc_d, u2.ravel())
+    np.testing.assert_array_equal(d.view(np.float32)[m], carried[m])
+    took_back = m & (u2.ravel() < acc_d)
+    assert took_back.sum() > 100
+    assert (wt[took_back] == -1).all() and (wr[took_back] == 0xFFFFFFFF).all()
+    orc.refine_voxels(g, V, T, vox, rp, F, d, fr, bk, wr, wt)
+    new = fresh(F, u2)
+    np.testing.assert_array_equal(d.view(np.float32)[m], np.minimum(carried, new[0])[m])
+    np.testing.assert_array_equal(fr, state[1].ravel() + new[1])
+    np.testing.assert_array_equal(bk, state[2].ravel() + new[2])
+
+
+def test_fine_representative_triangles_two_resolutions(orc):
+    """Sec. 2.5.1 two resolutions, sign fallback of the fine grid: each fine voxel takes
+    the representative triangle of the flooded seed of the coarse voxel that contains
+    its centre.  Ratio 1 is the one-grid gather rep_tri[nearest]; with ratio 2 on
+    ragged grids the containing coarse voxel is found from FP64 world coordinates, the
+    result is the coarse seed voxel's own representative, whose triangle overlaps that
+    seed voxel's cube, and an empty seed gives -1."""
+    V, T = scenes.icosphere(2)
+    V = (V * 0.3 + 0.5).astype(np.float32)
+    gf = scenes.Grid(33, 30, 35, (0.0, 0.0, 0.0), 1.0 / 32)
+    vv = orc.to_voxel(V, gf)
+    seed, rep, _ = orc.voxelize(vv, T, gf)
+    near = orc.jfa(gf, seed, scenes.jfa_steps(gf))
+
+    def fine_rep(gfine, gcoarse, ratio, near_c, rep_c):
+        out = np.empty(gfine.shape_zyx, dtype=np.int32)
+        orc.lib().or_fine_rep_2res(orc.C.byref(orc._g(gfine)), orc.C.byref(orc._g(gcoarse)), ratio,
+                                   orc._p(orc._i32(near_c)), orc._p(orc._i32(rep_c)), orc._p(out))
+        return out
+
+    r1 = fine_rep(gf, gf, 1, near, rep)
+    sx, sy, sz = near & 1023, (near >> 10) & 1023, near >> 20
+    np.testing.assert_array_equal(r1, np.where(near < 0, -1, rep[sz, sy, sx]))
+    gc = scenes.Grid(17, 15, 18, (0.0, 0.0, 0.0), 2.0 / 32)
+    vc = orc.to_voxel(V, gc)
+    seed_c, rep_c, _ = orc.voxelize(vc, T, gc)
+    near_c = orc.jfa(gc, seed_c, scenes.jfa_steps(gc))
+    near_c[3, :, :5] = -1                        # a patch no seed reached
+    r2 = fine_rep(gf, gc, 2, near_c, rep_c)
+    hf, hc = 1.0 / 32, 2.0 / 32
+    for k in range(gf.nz):
+        for j in range(gf.ny):
+            for i in range(gf.nx):
+                ci, cj, ck = (int(math.floor((n + 0.5) * hf / hc)) for n in (i, j, k))
+                s = int(near_c[ck, cj, ci])
+                if s < 0:
+                    assert r2[k, j, i] == -1
+                    continue
+                qx, qy, qz = s & 1023, (s >> 10) & 1023, s >> 20
+                assert r2[k, j, i] == rep_c[qz, qy, qx]
+    assert (r2 == -1).sum() == 2 * 30 * 10     # coarse z-plane 3, x < 5: 2 fine planes x 30 rows x 10 columns
+    # every used representative overlaps its coarse seed voxel's closed cube
+    used = {}
+    for s in np.unique(near_c[near_c >= 0]):
+        qx, qy, qz = s & 1023, (s >> 10) & 1023, s >> 20
+        used[s] = rep_c[qz, qy, qx]
+    for s, t in list(used.items())[:400]:
+        qx, qy, qz = s & 1023, (s >> 10) & 1023, s >> 20
+        a, b, c = (vc[T[t][n]] for n in range(3))
+        assert orc.tri_box_overlap(a, b, c, (qx + 0.5, qy + 0.5, qz + 0.5), 0.5)
