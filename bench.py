@@ -216,6 +216,75 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ghosting (Sec. 2.5.1)
+
+def tri_dist64_many(p, A, B, C):
+    """FP64 distance from point p to each triangle (A[i], B[i], C[i]): the plane foot
+    when it lies inside the triangle, else the nearest of the three edges."""
+    import numpy as np
+    e1, e2, ap = B - A, C - A, p[None, :] - A
+    d00, d01, d11 = (e1 * e1).sum(1), (e1 * e2).sum(1), (e2 * e2).sum(1)
+    d20, d21 = (ap * e1).sum(1), (ap * e2).sum(1)
+    den = d00 * d11 - d01 * d01
+    ok = den > 1e-300
+    sden = np.where(ok, den, 1.0)
+    u = (d11 * d20 - d01 * d21) / sden
+    v = (d00 * d21 - d01 * d20) / sden
+    inside = ok & (u >= 0) & (v >= 0) & (u + v <= 1)
+    foot = A + u[:, None] * e1 + v[:, None] * e2
+    best = np.where(inside, np.linalg.norm(p[None, :] - foot, axis=1), np.inf)
+    for a, b in ((A, B), (B, C), (C, A)):
+        ab = b - a
+        L = (ab * ab).sum(1)
+        t = np.clip(((p[None, :] - a) * ab).sum(1) / np.where(L > 0, L, 1.0), 0.0, 1.0)
+        best = np.minimum(best, np.linalg.norm(p[None, :] - (a + t[:, None] * ab), axis=1))
+    return best
+
+
+def true_distance_f64(vv, tris, pts, reach: float, cell: float = 12.0):
+    """FP64 unsigned distance (voxel units) from each point to the mesh with voxel-space
+    vertices vv, for points known to lie within `reach` of some triangle: triangles
+    are binned by bounding box into cubic cells, and each point checks the cells its
+    reach box overlaps."""
+    import numpy as np
+    V = np.asarray(vv, dtype=np.float64)
+    T = np.asarray(tris, dtype=np.int64)
+    ok = (T >= 0).all(1) & (T < len(V)).all(1)
+    T = T[ok]
+    A, B, C = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    good = np.isfinite(A).all(1) & np.isfinite(B).all(1) & np.isfinite(C).all(1)
+    A, B, C = A[good], B[good], C[good]
+    lo = np.floor(np.minimum(np.minimum(A, B), C) / cell).astype(np.int64)
+    hi = np.floor(np.maximum(np.maximum(A, B), C) / cell).astype(np.int64)
+    bins: dict = {}
+    for t in range(len(A)):
+        for cz in range(lo[t, 2], hi[t, 2] + 1):
+            for cy in range(lo[t, 1], hi[t, 1] + 1):
+                for cx in range(lo[t, 0], hi[t, 0] + 1):
+                    bins.setdefault((cx, cy, cz), []).append(t)
+    out = np.full(len(pts), np.inf)
+    for n, p in enumerate(np.asarray(pts, dtype=np.float64)):
+        c0 = np.floor((p - reach) / cell).astype(np.int64)
+        c1 = np.floor((p + reach) / cell).astype(np.int64)
+        cand = [bins.get((cx, cy, cz), []) for cz in range(c0[2], c1[2] + 1)
+                for cy in range(c0[1], c1[1] + 1) for cx in range(c0[0], c1[0] + 1)]
+        ids = np.unique(np.concatenate([np.asarray(c, dtype=np.int64) for c in cand])) if cand else []
+        if len(ids):
+            out[n] = tri_dist64_many(p, A[ids], B[ids], C[ids]).min()
+    return out
+
+
+def ghost_stats(values, truth, tol: float = 1e-4) -> dict:
+    """Ghosting of a field at sampled voxels: the fraction whose value lies below the
+    current frame's true distance (by more than FP32 rounding, `tol` voxel), and the
+    mean error value - truth (voxels)."""
+    import numpy as np
+    v = np.asarray(values, dtype=np.float64)
+    t = np.asarray(truth, dtype=np.float64)
+    return {"ghost_fraction": float(np.mean(v < t - tol)) if len(v) else 0.0,
+            "mean_error_vox": float(np.mean(v - t)) if len(v) else 0.0, "samples": int(len(v))}
+
+
 # ------------------------------------------------------------------ GPU path
 
 def bench_dynamic(dev, frames: int = 120, warmup: int = 3) -> dict:

@@ -211,7 +211,6 @@ struct PassD {
 
 struct PassTable {
     int32_t n;
-    int32_t m20, m10;  // -2^20, -2^10 (see jfa_column_interior)
     PassD e[kMaxBatch];
 };
 
@@ -225,7 +224,7 @@ __global__ void __launch_bounds__(kJX* kJY) k_bjfa_pass(const __grid_constant__ 
     const PassD& e = p.e[lo];
     const int local = b - e.block_start;
     jfa_column(e.in, e.out, e.nx, e.ny, e.nz, e.k, e.nchunk, kChunk, local % e.gbx, (local / e.gbx) % e.gby,
-               local / (e.gbx * e.gby), p.m20, p.m10);
+               local / (e.gbx * e.gby));
 }
 
 // ------------------------------------------------------------------ coarse field + refine
@@ -447,8 +446,6 @@ rtsdf_status enqueue_jfa(const rtsdf_batch_plan& P, uint32_t* a, uint32_t* b, cu
     for (int p = 0; p < P.npasses; ++p) {
         PassTable pt;
         memset(&pt, 0, sizeof(pt));
-        pt.m20 = -(1 << 20);
-        pt.m10 = -(1 << 10);
         int32_t blocks = 0;
         for (int si = 0; si < P.S; ++si) {
             const rtsdf_batch_scene& sc = P.scenes[si];
@@ -466,7 +463,7 @@ rtsdf_status enqueue_jfa(const rtsdf_batch_plan& P, uint32_t* a, uint32_t* b, cu
             e.k = sc.steps[idx];
             const int nq = (e.nz + e.k - 1) / e.k;
             e.nchunk = (nq + kChunk - 1) / kChunk;
-            e.gbx = (e.nx + kJX - 1) / kJX;
+            e.gbx = jfa_xblocks(e.nx, e.k);
             e.gby = (e.ny + kJY - 1) / kJY;
             e.block_start = blocks;
             blocks += e.gbx * e.gby * e.k * e.nchunk;

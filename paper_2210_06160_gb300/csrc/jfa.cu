@@ -6,18 +6,16 @@
 
 namespace rtsdf {
 
-// m20 = -2^20 and m10 = -2^10 (see jfa_column_interior)
 __global__ void __launch_bounds__(kJX* kJY) k_jfa_pass(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                     int nx, int ny, int nz, int k, int nchunk, int chunk, int m20,
-                                                     int m10) {
-    jfa_column(in, out, nx, ny, nz, k, nchunk, chunk, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
+                                                     int nx, int ny, int nz, int k, int nchunk, int chunk) {
+    jfa_column(in, out, nx, ny, nz, k, nchunk, chunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int K>
 __global__ void __launch_bounds__(kJX* kJY) k_jfa_pass_grouped(const uint32_t* __restrict__ in,
                                                              uint32_t* __restrict__ out, int nx, int ny, int nz,
-                                                             int grp, int m20, int m10) {
-    jfa_column_grouped<K>(in, out, nx, ny, nz, grp, blockIdx.x, blockIdx.y, blockIdx.z, m20, m10);
+                                                             int grp) {
+    jfa_column_grouped<K>(in, out, nx, ny, nz, grp, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* steps, int32_t nsteps,
@@ -31,20 +29,19 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
         const int nq = (g.nz + k - 1) / k;
         const int nchunk = (nq + chunk - 1) / chunk;
         const bool pow2 = k >= 64 && k <= 256 && (k & (k - 1)) == 0;
+        const unsigned gx = (unsigned)jfa_xblocks(g.nx, k), gy = (unsigned)((g.ny + kJY - 1) / kJY);
         if (pow2 && nq <= kGroupMaxPlanes) {
             const int grp = kChunk / nq;
-            const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)((k + grp - 1) / grp));
-            const int m20 = -(1 << 20), m10 = -(1 << 10);
+            const dim3 grid(gx, gy, (unsigned)((k + grp - 1) / grp));
             if (k == 64)
-                k_jfa_pass_grouped<64><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
+                k_jfa_pass_grouped<64><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp);
             else if (k == 128)
-                k_jfa_pass_grouped<128><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
+                k_jfa_pass_grouped<128><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp);
             else
-                k_jfa_pass_grouped<256><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp, m20, m10);
+                k_jfa_pass_grouped<256><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp);
         } else {
-            const dim3 grid((g.nx + kJX - 1) / kJX, (g.ny + kJY - 1) / kJY, (unsigned)(k * nchunk));
-            k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, chunk, -(1 << 20),
-                                              -(1 << 10));
+            const dim3 grid(gx, gy, (unsigned)(k * nchunk));
+            k_jfa_pass<<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, k, nchunk, chunk);
         }
         RTSDF_LAUNCHED();
         uint32_t* t = src; src = dst; dst = t;

@@ -172,6 +172,30 @@ def test_jfa_random_seeds_and_shapes_parity():
             np.testing.assert_array_equal(out.cpu().numpy(), want)
 
 
+def test_jfa_lattice_and_plane_seeds_with_ties_parity():
+    """Seeds on a ground plane, a wall and a coarse lattice make many voxels
+    equidistant from several seeds, so the lower-packed-seed rule decides often;
+    widths that are not multiples of twice the offset leave ragged column pairs."""
+    for dims in [(100, 50, 100), (37, 29, 41), (257, 9, 6)]:
+        g = scenes.Grid(*dims, (0.0, 0.0, 0.0), 1.0)
+        k, j, i = np.meshgrid(np.arange(g.nz), np.arange(g.ny), np.arange(g.nx), indexing="ij")
+        on = (j == min(3, g.ny - 1)) | (i == g.nx // 3) | ((i % 7 == 0) & (j % 5 == 0) & (k % 9 == 0))
+        s = np.where(on, (k << 20) | (j << 10) | i, -1).astype(np.int32)
+        steps = scenes.jfa_steps(g, extra_one=True)
+        want = oracle.jfa(g, s, steps)
+        a, b = to_dev(s), torch.empty_like(to_dev(s))
+        out = rt.rtsdf_jfa(rt.make_grid(g), a, b, steps)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        # one pass at a time as well, so a mistake in any single offset shows up
+        cur = s
+        for kk in steps:
+            want1 = oracle.jfa_pass(g, cur, kk)
+            a, b = to_dev(cur), torch.empty_like(to_dev(cur))
+            got1 = rt.rtsdf_jfa(rt.make_grid(g), a, b, [kk]).cpu().numpy()
+            np.testing.assert_array_equal(got1, want1, err_msg=f"dims {dims} offset {kk}")
+            cur = want1
+
+
 def test_empty_mesh_gives_empty_field_and_full_light():
     g = scenes.Grid(16, 12, 10, (0.0, 0.0, 0.0), 0.1)
     sc = scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), g,
