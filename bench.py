@@ -29,10 +29,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SDF rebuild ms/frame @400x200x400, GVoxel/s, %HBM roof; bwd+batch vs plain"
-JFA_ROOM_DRAM_BYTES_PER_FRAME = 2_209_870_592
-# smsp__inst_executed.sum of k_refine for one room frame (8 rays, 7.24 M masked voxels), from one
-# ncu capture of this kernel version; the refine kernel is bound by instruction issue, not bytes
-REFINE_ROOM_WARP_INSTR_PER_FRAME = 3_805_157_363
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the ten flooding passes of one
+# room frame, from one ncu capture, with the SHA-256 (first 16 hex digits) of the flooding
+# sources it was taken on; the bench reports it only while those sources are unchanged
+JFA_ROOM_TRAFFIC = {"bytes_per_frame": 2_214_624_512, "sources_sha256_16": "a1564cbf502b20cb"}
+JFA_SOURCES = ("paper_2210_06160_gb300/csrc/jfa_core.cuh", "paper_2210_06160_gb300/csrc/jfa.cu")
+# algorithmic operations per unit of refinement work (counted by the kernel in rtsdf_counters):
+# a ray is a Philox4x32-10 draw and Marsaglia's direction (about 20 FP32 and 40 integer
+# operations); a BVH child-box test about 25; a (voxel, triangle) reach test 7 (a squared
+# distance and a compare); a (pair, ray) plane/sphere filter test 10; a Moller-Trumbore test 35
+REFINE_OPS_PER_UNIT = {"ray": 60, "node_test": 25, "reach_test": 7, "filter_ray_test": 10, "exact_test": 35}
+
+
+def sources_hash(paths) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -150,44 +165,80 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_frame_sample(sc, seconds_hint: float = 10.0) -> dict:
-    """The oracle as it stands on a bounded sample of one frame, scaled to a full
-    frame: full voxelize, all JFA passes, full resolve, ray sampling of a subset of
-    masked voxels (scaled to all masked voxels), and the shadow of a subset of
-    receivers (scaled to all)."""
+def oracle_frame_sample(sc, threads: int | None = None, n_refine: int | None = None, full: bool = False) -> dict:
+    """The oracle as it stands, timed stage by stage on `threads` host threads (all
+    when None), on a bounded sample of one frame scaled to the whole frame: voxelize
+    and resolve in full; the flooding passes in full (all threads) or the first and
+    last pass scaled to all of them (one thread); ray sampling of `n_refine` masked
+    voxels (brute force over every triangle per ray) scaled to all masked voxels; the
+    shadow of a prefix of the receivers, scaled.  `full` runs everything in full (the
+    small workloads)."""
     import numpy as np
 
     import oracle
     g, rp = sc.grid, sc.refine
-    t = {}
+    nproc = os.cpu_count() or 1
+    oracle.set_num_threads(threads or nproc)
+    used = oracle.num_threads()
+    single = used == 1
+    t, note = {}, []
     t0 = time.perf_counter()
     vv = oracle.to_voxel(sc.verts, g)
     seed, rep, _ = oracle.voxelize(vv, sc.tris, g)
     t["voxelize"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    near = oracle.jfa(g, seed, sc.jfa_steps)
-    t["jfa"] = time.perf_counter() - t0
+    steps = list(sc.jfa_steps)
+    if full or not single:
+        t0 = time.perf_counter()
+        near = oracle.jfa(g, seed, steps)
+        t["jfa"] = time.perf_counter() - t0
+    else:
+        # one thread: time the first and the last pass (the cheapest and the dearest), scale
+        near = seed
+        t0 = time.perf_counter()
+        first = oracle.jfa_pass(g, seed, steps[0])
+        t_first = time.perf_counter() - t0
+        oracle.set_num_threads(nproc)
+        near = oracle.jfa(g, first, steps[1:])  # the field for resolve, not timed (all threads)
+        oracle.set_num_threads(used)
+        t0 = time.perf_counter()
+        oracle.jfa_pass(g, near, steps[-1])
+        t_last = time.perf_counter() - t0
+        t["jfa"] = 0.5 * (t_first + t_last) * len(steps)
+        note.append(f"JFA: passes {steps[0]} and {steps[-1]} timed, scaled to {len(steps)}")
     t0 = time.perf_counter()
     u_c, mask = oracle.resolve(g, vv, sc.tris, near, rep, rp.mask_vox)
     t["resolve"] = time.perf_counter() - t0
     masked = np.flatnonzero(mask.ravel()).astype(np.int32)
-    nsub = max(1, min(len(masked), 48 if len(sc.tris) > 10000 else 4096))
+    nsub = len(masked) if (full or n_refine is None or n_refine >= len(masked)) else max(1, n_refine)
     sub = masked[:: max(1, len(masked) // nsub)][:nsub]
     d, f, b = (x.ravel() for x in oracle.init_refine_state(u_c, mask)[:3])
     t0 = time.perf_counter()
     oracle.refine_voxels(g, vv, sc.tris, sub, rp, 0, d, f, b)
     t["refine"] = (time.perf_counter() - t0) * len(masked) / max(1, len(sub))
     sdf = (u_c - np.float32(rp.beta_vox)).astype(np.float32)
-    npix = min(len(sc.recv_pos), 50_000)
+    npix = len(sc.recv_pos) if full else min(len(sc.recv_pos), 50_000 if not single else 10_000)
     t0 = time.perf_counter()
     oracle.shadow(g, sdf, sc.recv_pos[:npix], sc.recv_nrm[:npix], sc.shadow)
-    t["shadow"] = (time.perf_counter() - t0) * len(sc.recv_pos) / npix
+    t["shadow"] = (time.perf_counter() - t0) * len(sc.recv_pos) / max(1, npix)
+    oracle.set_num_threads(nproc)
     total_ms = 1e3 * sum(t.values())
-    return {"value": total_ms, "unit": "ms/frame", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"full voxelize + JFA ({len(sc.jfa_steps)} passes) + resolve; ray sampling "
-                       f"of {len(sub)} of {len(masked)} masked voxels scaled; shadow of {npix} of "
-                       f"{len(sc.recv_pos)} receivers scaled"),
-            "stage_s": {k: round(v, 3) for k, v in t.items()}}
+    sample = (f"voxelize + resolve in full; JFA ({len(steps)} passes) "
+              + ("in full" if not note else "first and last pass scaled")
+              + f"; ray sampling of {len(sub)} of {len(masked)} masked voxels (brute force over {len(sc.tris)} "
+              f"triangles per ray){'' if len(sub) == len(masked) else ' scaled'}; shadow of {npix} of "
+              f"{len(sc.recv_pos)} receivers{'' if npix == len(sc.recv_pos) else ' scaled'}")
+    return {"value": total_ms, "unit": "ms/frame", "cores": used, "nproc": nproc, "kind": "oracle",
+            "sample": sample, "refined_voxels": int(len(sub)), "stage_s": {k: round(v, 3) for k, v in t.items()}}
+
+
+def cpu_baseline(sc, workload: str) -> dict:
+    """The oracle on all host threads (ray sampling of at least 4,096 masked voxels) and
+    on one thread (a smaller sample), both scaled to one frame."""
+    full = workload != "room"
+    allc = oracle_frame_sample(sc, None, n_refine=4096, full=full)
+    one = oracle_frame_sample(sc, 1, n_refine=96, full=full)
+    allc["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample", "stage_s")}
+    return allc
 
 
 def run_reference(args):
@@ -195,12 +246,14 @@ def run_reference(args):
     if rank != 0:
         return
     sc = load_scene(args.workload)
+    # each step a bounded sample of the frame (512 ray-sampled voxels on the room), all host threads
+    n_ref = 512 if args.workload == "room" else None
     for _ in range(args.warmup):
-        oracle_frame_sample(sc)
+        oracle_frame_sample(sc, None, n_refine=n_ref, full=args.workload != "room")
     vals, stage = [], None
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r = oracle_frame_sample(sc)
+        r = oracle_frame_sample(sc, None, n_refine=n_ref, full=args.workload != "room")
         vals.append(r["value"])
         stage = r
     wall = time.perf_counter() - t0
@@ -209,8 +262,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(sc, args.workload),
-            "cpu_baseline": {"value": v, "unit": "ms/frame", "cores": stage["cores"], "kind": "oracle",
-                             "sample": stage["sample"]},
+            "cpu_baseline": {"value": v, "unit": "ms/frame", "cores": stage["cores"], "nproc": stage["nproc"],
+                             "kind": "oracle", "sample": stage["sample"]},
             "e2e": {"value": v, "unit": "ms/frame", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 2)}
     print(json.dumps(line), flush=True)
@@ -218,11 +271,11 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ghosting (Sec. 2.5.1)
 
-def tri_dist64_many(p, A, B, C):
-    """FP64 distance from point p to each triangle (A[i], B[i], C[i]): the plane foot
-    when it lies inside the triangle, else the nearest of the three edges."""
+def tri_dist64_pairs(P, A, B, C):
+    """FP64 distance from point P[i] to triangle (A[i], B[i], C[i]), for every i: the
+    plane foot when it lies inside the triangle, else the nearest of the three edges."""
     import numpy as np
-    e1, e2, ap = B - A, C - A, p[None, :] - A
+    e1, e2, ap = B - A, C - A, P - A
     d00, d01, d11 = (e1 * e1).sum(1), (e1 * e2).sum(1), (e2 * e2).sum(1)
     d20, d21 = (ap * e1).sum(1), (ap * e2).sum(1)
     den = d00 * d11 - d01 * d01
@@ -232,45 +285,47 @@ def tri_dist64_many(p, A, B, C):
     v = (d00 * d21 - d01 * d20) / sden
     inside = ok & (u >= 0) & (v >= 0) & (u + v <= 1)
     foot = A + u[:, None] * e1 + v[:, None] * e2
-    best = np.where(inside, np.linalg.norm(p[None, :] - foot, axis=1), np.inf)
+    best = np.where(inside, np.linalg.norm(P - foot, axis=1), np.inf)
     for a, b in ((A, B), (B, C), (C, A)):
         ab = b - a
         L = (ab * ab).sum(1)
-        t = np.clip(((p[None, :] - a) * ab).sum(1) / np.where(L > 0, L, 1.0), 0.0, 1.0)
-        best = np.minimum(best, np.linalg.norm(p[None, :] - (a + t[:, None] * ab), axis=1))
+        t = np.clip(((P - a) * ab).sum(1) / np.where(L > 0, L, 1.0), 0.0, 1.0)
+        best = np.minimum(best, np.linalg.norm(P - (a + t[:, None] * ab), axis=1))
     return best
 
 
-def true_distance_f64(vv, tris, pts, reach: float, cell: float = 12.0):
+def true_distance_f64(vv, tris, pts, reach: float, small: float = 8.0):
     """FP64 unsigned distance (voxel units) from each point to the mesh with voxel-space
-    vertices vv, for points known to lie within `reach` of some triangle: triangles
-    are binned by bounding box into cubic cells, and each point checks the cells its
-    reach box overlaps."""
+    vertices vv, for points known to lie within `reach` of some triangle.  Triangles
+    of circumradius-about-centroid up to `small` are found through a k-d tree of their
+    centroids; larger ones are tested against every point."""
     import numpy as np
+    from scipy.spatial import cKDTree
     V = np.asarray(vv, dtype=np.float64)
     T = np.asarray(tris, dtype=np.int64)
-    ok = (T >= 0).all(1) & (T < len(V)).all(1)
-    T = T[ok]
+    T = T[(T >= 0).all(1) & (T < len(V)).all(1)]
     A, B, C = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
     good = np.isfinite(A).all(1) & np.isfinite(B).all(1) & np.isfinite(C).all(1)
     A, B, C = A[good], B[good], C[good]
-    lo = np.floor(np.minimum(np.minimum(A, B), C) / cell).astype(np.int64)
-    hi = np.floor(np.maximum(np.maximum(A, B), C) / cell).astype(np.int64)
-    bins: dict = {}
-    for t in range(len(A)):
-        for cz in range(lo[t, 2], hi[t, 2] + 1):
-            for cy in range(lo[t, 1], hi[t, 1] + 1):
-                for cx in range(lo[t, 0], hi[t, 0] + 1):
-                    bins.setdefault((cx, cy, cz), []).append(t)
-    out = np.full(len(pts), np.inf)
-    for n, p in enumerate(np.asarray(pts, dtype=np.float64)):
-        c0 = np.floor((p - reach) / cell).astype(np.int64)
-        c1 = np.floor((p + reach) / cell).astype(np.int64)
-        cand = [bins.get((cx, cy, cz), []) for cz in range(c0[2], c1[2] + 1)
-                for cy in range(c0[1], c1[1] + 1) for cx in range(c0[0], c1[0] + 1)]
-        ids = np.unique(np.concatenate([np.asarray(c, dtype=np.int64) for c in cand])) if cand else []
-        if len(ids):
-            out[n] = tri_dist64_many(p, A[ids], B[ids], C[ids]).min()
+    P = np.asarray(pts, dtype=np.float64)
+    cen = (A + B + C) / 3.0
+    rad = np.sqrt(np.maximum(np.maximum(((A - cen) ** 2).sum(1), ((B - cen) ** 2).sum(1)), ((C - cen) ** 2).sum(1)))
+    big = np.flatnonzero(rad > small)
+    sm = np.flatnonzero(rad <= small)
+    pp, tt = [], []
+    if len(sm):
+        lists = cKDTree(cen[sm]).query_ball_point(P, reach + float(rad[sm].max()))
+        cnt = np.array([len(l) for l in lists])
+        pp.append(np.repeat(np.arange(len(P)), cnt))
+        tt.append(sm[np.concatenate([np.asarray(l, dtype=np.int64) for l in lists])] if cnt.sum() else
+                  np.zeros(0, np.int64))
+    if len(big):
+        pp.append(np.repeat(np.arange(len(P)), len(big)))
+        tt.append(np.tile(big, len(P)))
+    out = np.full(len(P), np.inf)
+    if pp:
+        pi, ti = np.concatenate(pp), np.concatenate(tt)
+        np.minimum.at(out, pi, tri_dist64_pairs(P[pi], A[ti], B[ti], C[ti]))
     return out
 
 
@@ -287,12 +342,20 @@ def ghost_stats(values, truth, tol: float = 1e-4) -> dict:
 
 # ------------------------------------------------------------------ GPU path
 
-def bench_dynamic(dev, frames: int = 120, warmup: int = 3) -> dict:
+def bench_dynamic(dev, frames: int = 120, warmup: int = 3, ghost_every: int = 4, ghost_samples: int = 16384) -> dict:
     """The room animated over `frames` frames (seeded linear and angular motion, 10
     deforming primitives): every frame re-voxelizes, rebuilds the BVH, floods and refines
     with 4 rays per voxel, then shades 1920x1080 receivers. Per-frame vertex arrays
-    are uploaded before timing; each frame is timed with events. Run twice: fresh per
-    frame (no carry-over) and with the Eq. (1) decay (alpha 0.95)."""
+    are uploaded before timing; each frame is timed with events. Run three ways: fresh
+    per frame (no carry-over), with the Eq. (1) decay (alpha 0.95), and with the plain
+    minimum over frames (the accumulation of the static scene).
+
+    Ghosting (Sec. 2.5.1): on every `ghost_every`-th frame, seeded uniform voxels are read
+    back after the frame (outside its timed span); at those inside the frame's ray mask
+    the refined distance is compared with the FP64 distance to that frame's mesh.  The
+    ghost fraction is the share below it (by more than FP32 rounding): distances left
+    over from where a surface was.  Fresh frames cannot ghost (every value is a hit
+    distance or a coarse distance on the current mesh); the decay fades old values."""
     import numpy as np
     import torch
 
@@ -301,17 +364,24 @@ def bench_dynamic(dev, frames: int = 120, warmup: int = 3) -> dict:
 
     anim = scenes.room_animation()
     sc = anim.scene
-    verts = [torch.from_numpy(scenes.room_frame(anim, f)).to(dev) for f in range(frames)]
+    g = sc.grid
+    host_verts = [scenes.room_frame(anim, f) for f in range(frames)]
+    verts = [torch.from_numpy(v).to(dev) for v in host_verts]
     tris = torch.from_numpy(sc.tris).to(dev)
     pos = torch.from_numpy(sc.recv_pos).to(dev)
     nrm = torch.from_numpy(sc.recv_nrm).to(dev)
-    P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), device=dev)
+    P = rt.Pipeline(g, len(sc.verts), len(sc.tris), device=dev)
     vis = torch.empty(len(sc.recv_pos), dtype=torch.float32, device=dev)
     sp = rt.make_shadow_params(sc.shadow)
     stream = torch.cuda.current_stream()
+    ghost_frames = list(range(0, frames, ghost_every))
+    rng = np.random.default_rng(2510)
+    samples = {f: np.sort(rng.choice(g.nvox, ghost_samples, replace=False)) for f in ghost_frames}
+    sample_dev = {f: torch.from_numpy(samples[f].astype(np.int64)).to(dev) for f in ghost_frames}
     out = {"workload": (f"room 400x200x400 animated, {frames} frames, {len(sc.tris)} triangles, "
                         f"{sc.refine.rays_per_voxel} rays/voxel, full rebuild + 1920x1080 shadow per frame")}
-    for label, mode in (("fresh", 0), ("decay", 2)):
+    reads = {}
+    for label, mode in (("fresh", 0), ("decay", 2), ("minimum", 1)):
         def frame(f):
             rp = rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f,
                                                            accumulate=mode if f > 0 else 0))
@@ -322,16 +392,48 @@ def bench_dynamic(dev, frames: int = 120, warmup: int = 3) -> dict:
             frame(f)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+        got = {}
         for f in range(frames):
             evs[f][0].record(stream)
             frame(f)
             evs[f][1].record(stream)
+            if f in sample_dev:
+                got[f] = (P.dist_bits.view(-1).index_select(0, sample_dev[f]),
+                          P.nearest.view(-1).index_select(0, sample_dev[f]))
         torch.cuda.synchronize()
         ms = np.array([a.elapsed_time(b) for a, b in evs])
         out[label] = {"p50_ms": round(float(np.percentile(ms, 50)), 4), "p99_ms": round(float(np.percentile(ms, 99)), 4),
                       "mean_ms": round(float(ms.mean()), 4), "max_ms": round(float(ms.max()), 4)}
+        reads[label] = {f: (d.cpu().numpy().view(np.uint32).view(np.float32), n.cpu().numpy()) for f, (d, n) in got.items()}
     del P, verts
     torch.cuda.empty_cache()
+    # FP64 truth at the masked samples of each read frame (the same for every mode)
+    D = float(sc.refine.mask_vox)
+    per_frame = {label: [] for label in reads}
+    errs = {label: [] for label in reads}
+    n_masked = 0
+    for f in ghost_frames:
+        lin = samples[f]
+        k, j, i = lin // (g.nx * g.ny), (lin // g.nx) % g.ny, lin % g.nx
+        s = reads["fresh"][f][1].astype(np.int64)
+        d2 = (i - (s & 1023)) ** 2 + (j - ((s >> 10) & 1023)) ** 2 + (k - (s >> 20)) ** 2
+        m = (s >= 0) & (d2 <= D * D)  # the frame's ray mask (the same seeds in every mode)
+        pts = np.stack([i[m], j[m], k[m]], 1) + 0.5
+        vv = (host_verts[f].astype(np.float64) - np.array(g.origin)) / g.h
+        truth = true_distance_f64(vv, sc.tris, pts, reach=D + 1.0)
+        n_masked += int(m.sum())
+        for label in reads:
+            val = reads[label][f][0][m]
+            st = ghost_stats(val, truth)
+            per_frame[label].append(round(st["ghost_fraction"], 5))
+            errs[label].append(st["mean_error_vox"])
+    out["ghosting"] = {
+        "frames_read": ghost_frames, "samples_per_frame": ghost_samples, "masked_samples": n_masked,
+        "definition": ("share of sampled masked voxels whose refined distance is below the FP64 distance to the "
+                       "current frame's mesh by more than 1e-4 voxel; mean error = refined - FP64 truth (voxels)"),
+        **{f"ghosting_{label}": {"mean": round(float(np.mean(v)), 5), "max": round(float(np.max(v)), 5),
+                                 "per_frame": v, "mean_error_vox": round(float(np.mean(errs[label])), 4)}
+           for label, v in per_frame.items()}}
     return out
 
 
@@ -647,6 +749,13 @@ def run_ours(args):
         dist.barrier()
     launches = rt.rtsdf_kernel_launches() - n_launch0
     clk = clocks.stop()
+    # one more frame, outside the timed region, with the refinement counting its work units
+    work0 = rt.counters_dict(P.counters)
+    P.refine(verts, tris, rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f, accumulate=True),
+                                                count_work=True), stream)
+    torch.cuda.synchronize()
+    f += 1
+    work1 = rt.counters_dict(P.counters)
     t_ms = max_over_ranks(start.elapsed_time(end), world, dev)
     def span(a, b):
         return statistics.mean(evs[i][a].elapsed_time(evs[i][b]) for i in range(args.steps))
@@ -668,28 +777,40 @@ def run_ours(args):
         hbm_peak, peak_src = 6800.0, "fallback"
     jfa_bytes = 8.0 * nvox * len(sc.jfa_steps)  # 4 B read + 4 B write per voxel per pass
     jfa_gbs = jfa_bytes / (stage["jfa"] * 1e-3) / 1e9
-    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the ten passes of one
-    # room frame, from one ncu capture of this kernel version
-    traffic = JFA_ROOM_DRAM_BYTES_PER_FRAME if args.workload == "room" else None
+    # DRAM traffic of the passes from one ncu capture, while the flooding sources are the ones captured
+    traffic = None
+    if args.workload == "room" and JFA_ROOM_TRAFFIC["sources_sha256_16"] == sources_hash(JFA_SOURCES):
+        traffic = JFA_ROOM_TRAFFIC["bytes_per_frame"]
     roofline = {"kernel": "k_jfa_pass + k_jfa_pass_grouped (all passes of a frame)", "bound": "hbm", "achieved": round(jfa_gbs, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(jfa_gbs / hbm_peak, 4), "traffic": traffic,
                 "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes,
-                "limit": "integer ALU and FMA-heavy pipes (half-rate), not HBM"}
+                "limit": "instruction issue (27 candidates per voxel, an exact (distance, seed) argmin each), not HBM"}
 
-    # the dominant kernel by time, k_refine, is issue-bound: warp-instructions per second against
-    # four schedulers per SM at the sampled SM clock; timed by the refine stage, which also holds
-    # k_resolve and k_refine_report, so the rate is a lower bound on k_refine's own
-    roofline_refine = None
-    if args.workload == "room":
-        sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
-        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        issue_peak = 4.0 * nsm * sm_mhz * 1e6 / 1e9
-        issue_rate = REFINE_ROOM_WARP_INSTR_PER_FRAME / (stage["refine"] * 1e-3) / 1e9
-        roofline_refine = {"kernel": "k_refine (timed with k_resolve in the refine stage)", "bound": "issue",
-                           "achieved": round(issue_rate, 1), "peak": round(issue_peak, 1),
-                           "unit": "G warp-instructions/s", "frac": round(issue_rate / issue_peak, 4),
-                           "warp_instructions_per_frame": REFINE_ROOM_WARP_INSTR_PER_FRAME,
-                           "peak_source": f"4 schedulers x {nsm} SMs x median SM clock {sm_mhz:.0f} MHz"}
+    # the dominant kernel by time, k_refine: the work it counts (rtsdf_counters, one counted frame)
+    # per frame, as rates and as algorithmic operations per second against the FP32 lanes' rate at
+    # the sampled SM clock; timed by the refine stage of the timed (uncounted) frames, which also
+    # holds k_resolve and k_refine_report, so the rates are lower bounds on k_refine's own
+    sm_mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    wide = ("node_tests", "reach_tests", "filter_pairs", "exact_tests")  # 64-bit counters; the others wrap at 2^32
+    per_frame = {k: ((work1[k] - work0[k]) if k in wide else (work1[k] - work0[k]) & 0xFFFFFFFF)
+                 for k in ("masked_voxels", "rays_hit", "near_edge_hits") + wide}
+    units = {"ray": per_frame["masked_voxels"] * sc.refine.rays_per_voxel, "node_test": per_frame["node_tests"],
+             "reach_test": per_frame["reach_tests"],
+             "filter_ray_test": per_frame["filter_pairs"] * sc.refine.rays_per_voxel,
+             "exact_test": per_frame["exact_tests"]}
+    ops = sum(units[u] * REFINE_OPS_PER_UNIT[u] for u in units)
+    t_ref = stage["refine"] * 1e-3
+    lane_peak = 128.0 * nsm * sm_mhz * 1e6  # FP32 lanes per SM x SMs x clock: one operation each per cycle
+    roofline_refine = {"kernel": "k_refine (timed with k_resolve in the refine stage)", "bound": "alu",
+                       "achieved": round(ops / t_ref / 1e12, 3), "peak": round(lane_peak / 1e12, 3),
+                       "unit": "T lane-operations/s", "frac": round(ops / t_ref / lane_peak, 4),
+                       "peak_source": f"128 FP32 lanes x {nsm} SMs x median SM clock {sm_mhz:.0f} MHz",
+                       "ops_per_unit": REFINE_OPS_PER_UNIT,
+                       "units_per_frame": {k: int(v) for k, v in units.items()},
+                       "rates_per_s": {f"{k}s": round(v / t_ref, 1) for k, v in units.items()},
+                       "near_edge_hits_per_frame": per_frame["near_edge_hits"],
+                       "rays_hit_per_frame": per_frame["rays_hit"]}
 
     counters = rt.counters_dict(P.counters)
 
@@ -770,7 +891,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_frame_sample(sc)
+        cpu = cpu_baseline(sc, args.workload)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "ms/frame", "n_gpus": world,

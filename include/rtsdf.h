@@ -74,6 +74,9 @@ typedef struct {
                                temporal accumulation); 2: decayed accumulation of Eq. (1), see rtsdf_refine */
     int32_t sign_fallback;  /* 1: front == back -> side of the representative triangle's plane */
     float decay_alpha;      /* alpha of Eq. (1) (accumulate = 2), in [0, 1] */
+    int32_t count_work;     /* nonzero: also count the work units and near-edge hits of the ray sampling
+                               into the counters' node_tests ... exact_tests and near_edge_hits (about 3%
+                               slower; rtsdf_refine_tracked and the batch never count them) */
 } rtsdf_refine_params;
 
 /* Soft-shadow raymarch (Sec. 2.4, 2.5.2, 2.5.3); distances in voxels. */
@@ -91,14 +94,30 @@ typedef struct {
                                 key (0x51AD0, 0x7E2): the top 24 bits of the first word times 2^-24 */
 } rtsdf_shadow_params;
 
-/* Device-side counters; each call adds to the fields it owns. */
+/* Device-side counters; each call adds to the fields it owns.  The caller zeroes
+ * the block and reads it back; it must be 8-byte aligned.  The 64-bit fields count
+ * the refinement's work (Sec. 2.1), for throughput figures:
+ *   node_tests   BVH child boxes tested against a brick's reach region,
+ *   reach_tests  (masked voxel, staged triangle) pairs tested for reach,
+ *   filter_pairs pairs within reach, each then filtered against every ray of the voxel,
+ *   exact_tests  (ray, triangle) pairs given the exact Moller-Trumbore test.
+ * near_edge_hits counts the exact-test hits whose smallest barycentric coordinate
+ * (u, w or 1 - u - w, as the test computes them in FP32) is below 1e-6: the hits a
+ * different rounding of the same arithmetic could turn into misses.  It counts hits
+ * over every tested triangle, not only each ray's closest, so it equals the count
+ * of a brute-force test of every (ray, triangle) pair. */
 typedef struct {
     uint32_t skipped_triangles; /* voxelize / build_bvh: invalid triangles */
     uint32_t masked_voxels;     /* refine: voxels inside the ray mask */
     uint32_t rays_hit;          /* refine: rays with a hit */
     uint32_t rays_failed;       /* refine: rays with no direction after 32 Philox draws */
     uint32_t stack_overflow;    /* refine: traversals that overflowed the stack (result incomplete) */
-    uint32_t reserved[3];
+    uint32_t near_edge_hits;    /* refine: exact-test hits within 1e-6 (barycentric) of an edge */
+    uint32_t reserved[2];
+    uint64_t node_tests;        /* refine: BVH child-box tests */
+    uint64_t reach_tests;       /* refine: (voxel, triangle) reach tests */
+    uint64_t filter_pairs;      /* refine: (voxel, triangle) pairs filtered against the voxel's rays */
+    uint64_t exact_tests;       /* refine: exact ray/triangle tests */
 } rtsdf_counters;
 
 /* ---------------------------------------------------------------- voxelize */

@@ -62,8 +62,8 @@ def lib():
                 "or_resolve": (None, [G, P, P, P, P, f32, f32, P, P]),
                 "or_philox4x32_10": (None, [P, P, P]),
                 "or_sphere_dir": (C.c_int, [u32, u32, u32, P, P]),
-                "or_ray_tri": (C.c_int, [P, P, P, P, P, f32, P, P]),
-                "or_refine_voxels": (i64, [G, P, i32, P, i32, P, i64, i32, f32, P, u32, u32, P, P, P, P, P]),
+                "or_ray_tri": (C.c_int, [P, P, P, P, P, f32, P, P, P]),
+                "or_refine_voxels": (i64, [G, P, i32, P, i32, P, i64, i32, f32, P, u32, u32, P, P, P, P, P, P]),
                 "or_vote_sign": (C.c_int, [u32, u32, P, P, P, P, C.c_int]),
                 "or_finalize": (None, [G, P, P, P, P, P, P, P, P, P, f32, C.c_int, P]),
                 "or_trilinear": (f32, [G, P, f32, f32, f32]),
@@ -73,6 +73,7 @@ def lib():
                 "or_shadow": (None, [G, P, P, P, i32, P, f32, i32, f32, f32, f32, f32, f32, P, P]),
                 "or_jitter_starts": (None, [i32, f32, f32, u32, P]),
                 "or_num_threads": (C.c_int, []),
+                "or_set_num_threads": (None, [C.c_int]),
                 "or_frozen_sources": (None, [G, P, P, P, P, P, P, P, P, P, P, u32, C.c_int, P]),
                 "or_frozen_sdf_f64": (None, [G, P, P, P, C.c_double, P]),
                 "or_frozen_sdf_backward_f64": (None, [G, P, P, P, C.c_double, P, P]),
@@ -103,6 +104,10 @@ def _i32(a) -> np.ndarray:
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().or_set_num_threads(int(n))
 
 
 def empty_dist(grid) -> float:
@@ -145,12 +150,15 @@ def sphere_dir(voxel: int, ray: int, scene: int, key) -> tuple[np.ndarray, int]:
     return d, att
 
 
-def ray_tri(o, d, a, b, c, tmax: float):
+def ray_tri(o, d, a, b, c, tmax: float, with_margin: bool = False):
+    """(hit, t, front), plus the hit's smallest barycentric coordinate with_margin."""
     o, d, a, b, c = _f32(o), _f32(d), _f32(a), _f32(b), _f32(c)
     t = np.zeros(1, dtype=np.float32)
     f = np.zeros(1, dtype=np.int32)
-    hit = lib().or_ray_tri(_p(o), _p(d), _p(a), _p(b), _p(c), float(tmax), _p(t), _p(f))
-    return (bool(hit), float(t[0]), bool(f[0])) if hit else (False, None, None)
+    m = np.zeros(1, dtype=np.float32)
+    hit = lib().or_ray_tri(_p(o), _p(d), _p(a), _p(b), _p(c), float(tmax), _p(t), _p(f), _p(m))
+    out = (bool(hit), float(t[0]), bool(f[0])) if hit else (False, None, None)
+    return out + ((float(m[0]) if hit else None),) if with_margin else out
 
 
 def sample(grid, sdf, pts) -> np.ndarray:
@@ -200,9 +208,12 @@ def resolve(grid, vv, tris, nearest, rep_tri, mask_vox: float):
     return u_c, mask
 
 
-def refine_voxels(grid, vv, tris, vox, rp, frame: int, dist_bits, front, back, win_ray=None, win_tri=None) -> int:
+def refine_voxels(grid, vv, tris, vox, rp, frame: int, dist_bits, front, back, win_ray=None, win_tri=None,
+                  near_edge=None) -> int:
     """Sec. 2.1 on the listed voxels; dist_bits/front/back (and the winner record
-    win_ray/win_tri when given) are updated in place."""
+    win_ray/win_tri when given) are updated in place.  near_edge (an int64 array of
+    one element, optional) receives the number of ray/triangle hits within 1e-6
+    (barycentric) of an edge.  Returns the rays whose direction could not be drawn."""
     vv, t, vox = _f32(vv), _i32(tris), _i32(vox)
     key = np.array(rp.key, dtype=np.uint32)
     for a in (dist_bits, front, back):
@@ -212,7 +223,8 @@ def refine_voxels(grid, vv, tris, vox, rp, frame: int, dist_bits, front, back, w
     return int(lib().or_refine_voxels(C.byref(_g(grid)), _p(vv), len(vv), _p(t), len(t), _p(vox),
                                       len(vox), int(rp.rays_per_voxel), float(rp.max_ray_vox),
                                       _p(key), frame & 0xFFFFFFFF, rp.scene_id & 0xFFFFFFFF,
-                                      _p(dist_bits), _p(front), _p(back), wr, wt))
+                                      _p(dist_bits), _p(front), _p(back), wr, wt,
+                                      None if near_edge is None else _p(near_edge)))
 
 
 def finalize(grid, vv, tris, nearest, rep_tri, mask, u_c, dist_bits, front, back, rp) -> np.ndarray:
@@ -335,16 +347,19 @@ def rebuild(scene, frames: int | None = None, frame0: int = 0, voxel_subset=None
     todo = masked if voxel_subset is None else np.intersect1d(masked, voxel_subset).astype(np.int32)
     state = None
     nf = scene.frames if frames is None else frames
+    near = np.zeros(1, dtype=np.int64)
+    near_total = 0
     for f in range(nf):
         state = init_refine_state(u_c, mask, state, accumulate=rp.accumulate, alpha=rp.decay_alpha)
         dist, fr, bk, wr, wt = (a.ravel() for a in state)
-        refine_voxels(g, vv, scene.tris, todo, rp, frame0 + f, dist, fr, bk, wr, wt)
+        refine_voxels(g, vv, scene.tris, todo, rp, frame0 + f, dist, fr, bk, wr, wt, near_edge=near)
+        near_total += int(near[0])
         state = tuple(a.reshape(g.shape_zyx) for a in (dist, fr, bk, wr, wt))
     dist, fr, bk, wr, wt = state
     sdf = finalize(g, vv, scene.tris, nearest, rep, mask, u_c, dist, fr, bk, rp)
     return dict(vv=vv, seed=seed, rep_tri=rep, skipped=skipped, nearest=nearest, u_c=u_c,
                 mask=mask, masked=masked, refined=todo, dist_bits=dist, front=fr, back=bk,
-                win_ray=wr, win_tri=wt, sdf=sdf)
+                win_ray=wr, win_tri=wt, sdf=sdf, near_edge=near_total)
 
 
 # ------------------------------------------------------------------ adjoint (FP64)

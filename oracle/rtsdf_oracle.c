@@ -18,6 +18,14 @@
 #include <omp.h>
 #endif
 
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -408,7 +416,7 @@ int or_sphere_dir(uint32_t voxel, uint32_t ray, uint32_t scene, const uint32_t k
 /* -------------------------------------------------------- ray / triangle */
 
 int or_ray_tri(const float o[3], const float d[3], const float* A, const float* B, const float* C,
-               float tmax, float* t, int* front) {
+               float tmax, float* t, int* front, float* margin) {
     float e1[3], e2[3], p[3], tv[3], q[3];
     sub3(B, A, e1);
     sub3(C, A, e2);
@@ -421,11 +429,17 @@ int or_ray_tri(const float o[3], const float d[3], const float* A, const float* 
     if (u < 0.0f || u > 1.0f) return 0;
     cross3(tv, e1, q);
     float w = dot3(d, q) * inv;
-    if (w < 0.0f || u + w > 1.0f) return 0;
+    float uw = u + w;
+    if (w < 0.0f || uw > 1.0f) return 0;
     float tt = dot3(e2, q) * inv;
     if (!(tt > 0.0f && tt <= tmax)) return 0;
     *t = tt;
     *front = det > 0.0f; /* det = -d.(e1 x e2): positive when the ray faces the outward normal */
+    if (margin) {
+        float m = u < w ? u : w;
+        float r = 1.0f - uw;
+        *margin = m < r ? m : r;
+    }
     return 1;
 }
 
@@ -435,11 +449,11 @@ int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int
                          const int32_t* vox, int64_t n, int32_t R, float tmax,
                          const uint32_t key[2], uint32_t frame, uint32_t scene,
                          uint32_t* dist_bits, uint32_t* front, uint32_t* back,
-                         uint32_t* win_ray, int32_t* win_tri) {
+                         uint32_t* win_ray, int32_t* win_tri, int64_t* near_edge) {
     uint8_t* ok = (uint8_t*)malloc((size_t)(T > 0 ? T : 1));
     for (int32_t t = 0; t < T; ++t) ok[t] = (uint8_t)tri_valid(vv, V, tris, t);
-    int64_t failed = 0;
-#pragma omp parallel for schedule(dynamic, 16) reduction(+ : failed)
+    int64_t failed = 0, near = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : failed, near)
     for (int64_t n_i = 0; n_i < n; ++n_i) {
         int32_t lin = vox[n_i];
         int i = lin % g->nx, j = (lin / g->nx) % g->ny, k = lin / (g->nx * g->ny);
@@ -463,11 +477,13 @@ int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int
             for (int32_t t = 0; t < T; ++t) {
                 if (!ok[t]) continue;
                 const int32_t* tr = tris + 3 * (int64_t)t;
-                float tt;
+                float tt, margin;
                 int f;
-                if (or_ray_tri(o, dir, vv + 3 * (int64_t)tr[0], vv + 3 * (int64_t)tr[1],
-                               vv + 3 * (int64_t)tr[2], tmax, &tt, &f) &&
-                    tt < best) { /* ascending ids: strict < keeps the lower id on ties */
+                if (!or_ray_tri(o, dir, vv + 3 * (int64_t)tr[0], vv + 3 * (int64_t)tr[1],
+                                vv + 3 * (int64_t)tr[2], tmax, &tt, &f, &margin))
+                    continue;
+                if (margin < 1e-6f) ++near;
+                if (tt < best) { /* ascending ids: strict < keeps the lower id on ties */
                     best = tt;
                     best_front = f;
                     best_tri = t;
@@ -493,6 +509,7 @@ int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int
         back[lin] = bk;
     }
     free(ok);
+    if (near_edge) *near_edge = near;
     return failed;
 }
 

@@ -78,9 +78,10 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 int or_sphere_dir(uint32_t voxel, uint32_t ray, uint32_t scene, const uint32_t key[2], float dir[3]);
 
 /* Ray / triangle (Moller-Trumbore).  Hit iff 0 < t <= tmax.  *front = 1 when the
- * ray meets the outward (counter-clockwise) side. */
+ * ray meets the outward (counter-clockwise) side.  On a hit, *margin (may be NULL)
+ * is the smallest of the barycentric coordinates u, w and 1 - (u + w). */
 int or_ray_tri(const float o[3], const float d[3], const float* a, const float* b, const float* c,
-               float tmax, float* t, int* front);
+               float tmax, float* t, int* front, float* margin);
 
 /* Sec. 2.1: ray-sampled refinement of the listed voxels by brute force over all
  * triangles.  For voxel vox[i], rays r = 0..R-1 get ray id frame*R + r; each ray's
@@ -88,13 +89,15 @@ int or_ray_tri(const float o[3], const float d[3], const float* a, const float* 
  * dist/front/back hold the incoming state (float bits) and are updated in place.
  * When this call's closest hit (t, then triangle id, then first ray) lowers dist,
  * win_ray/win_tri (may be NULL) record that ray id and triangle: the frozen source
- * of the refined distance used by the adjoint.
+ * of the refined distance used by the adjoint.  *near_edge (may be NULL) gets
+ * the number of (ray, triangle) hits, over every triangle, whose barycentric margin
+ * is below 1e-6.
  * Returns the number of rays whose direction could not be drawn. */
 int64_t or_refine_voxels(const or_grid* g, const float* vv, int32_t V, const int32_t* tris, int32_t T,
                          const int32_t* vox, int64_t n, int32_t R, float tmax,
                          const uint32_t key[2], uint32_t frame, uint32_t scene,
                          uint32_t* dist_bits, uint32_t* front, uint32_t* back,
-                         uint32_t* win_ray, int32_t* win_tri);
+                         uint32_t* win_ray, int32_t* win_tri, int64_t* near_edge);
 
 /* Sign of a refined voxel (Sec. 2.1): negative iff back > front; on a tie the side
  * of the representative triangle's plane decides when fallback != 0. Returns -1/+1. */
@@ -166,6 +169,8 @@ double or_shadow_loss_f64(const or_grid* g, const float* sdf32, const double* sd
                           float bias, const float* t_start, const float* target, double* gsdf, double* gl);
 
 /* Helpers for the tests: number of OpenMP threads the oracle uses. */
+/* OpenMP threads of the voxel-parallel loops (the timing baseline sets 1 or all). */
+void or_set_num_threads(int n);
 int or_num_threads(void);
 
 #endif

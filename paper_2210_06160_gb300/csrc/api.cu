@@ -64,7 +64,7 @@ rtsdf_status rtsdf_voxelize(const float* verts, int32_t V, const int32_t* tris, 
                             rtsdf_stream stream) {
     if (!grid_ok(g) || !mesh_ok(verts, V, tris, T)) return RTSDF_EINVAL;
     if (!buf_ok(seed, 16) || !buf_ok(rep_tri, 16) || !buf_ok(ws, 256)) return RTSDF_EINVAL;
-    if (counters && !aligned(counters, 4)) return RTSDF_EINVAL;
+    if (counters && !aligned(counters, 8)) return RTSDF_EINVAL;
     if (ws_bytes < voxelize_workspace(T, *g)) return RTSDF_ENOMEM;
     return voxelize(verts, V, tris, T, *g, seed, rep_tri, ws, counters, cs(stream));
 }
@@ -77,7 +77,7 @@ rtsdf_status rtsdf_build_bvh(const float* verts, int32_t V, const int32_t* tris,
                              rtsdf_stream stream) {
     if (!grid_ok(g) || !mesh_ok(verts, V, tris, T)) return RTSDF_EINVAL;
     if (!buf_ok(bvh, 256) || !buf_ok(ws, 256)) return RTSDF_EINVAL;
-    if (counters && !aligned(counters, 4)) return RTSDF_EINVAL;
+    if (counters && !aligned(counters, 8)) return RTSDF_EINVAL;
     if (bvh_bytes_ < bvh_bytes(T) || ws_bytes < bvh_workspace(T)) return RTSDF_ENOMEM;
     return build_bvh(verts, V, tris, T, *g, bvh, ws, counters, cs(stream));
 }
@@ -125,7 +125,7 @@ rtsdf_status refine_checked(const rtsdf_grid* g, const float* verts, int32_t V, 
     if (!buf_ok(bvh, 256) || !buf_ok(nearest, 16) || !buf_ok(rep_tri, 16) || !buf_ok(dist_bits, 16) ||
         !buf_ok(front, 16) || !buf_ok(back, 16) || !buf_ok(sdf_out, 16) || !buf_ok(ws, 256))
         return RTSDF_EINVAL;
-    if (counters && !aligned(counters, 4)) return RTSDF_EINVAL;
+    if (counters && !aligned(counters, 8)) return RTSDF_EINVAL;
     if (p->rays_per_voxel < 1 || p->rays_per_voxel > 4096) return RTSDF_EINVAL;
     if (p->accumulate < 0 || p->accumulate > 2) return RTSDF_EINVAL;
     if (p->accumulate == 2 && !(p->decay_alpha >= 0.0f && p->decay_alpha <= 1.0f)) return RTSDF_EINVAL;

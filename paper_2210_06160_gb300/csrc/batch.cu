@@ -764,7 +764,7 @@ rtsdf_status rtsdf_batch_set_tuning(rtsdf_batch_plan* plan, const rtsdf_batch_tu
 rtsdf_status rtsdf_batch_rebuild(rtsdf_batch_plan* plan, const rtsdf_batch_buffers* b, uint32_t frame_index,
                                  int32_t accumulate, rtsdf_counters* counters, rtsdf_stream stream) {
     RTSDF_TRY(buffers_ok(plan, b));
-    if (counters && reinterpret_cast<uintptr_t>(counters) % 4) return RTSDF_EINVAL;
+    if (counters && reinterpret_cast<uintptr_t>(counters) % 8) return RTSDF_EINVAL;
     if (accumulate < 0 || accumulate > 2) return RTSDF_EINVAL;
     if (accumulate == 2)
         for (const rtsdf_batch_scene& sc : plan->scenes)

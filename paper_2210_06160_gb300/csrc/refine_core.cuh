@@ -170,7 +170,7 @@ __device__ __forceinline__ bool box_near(float4 lo, float4 hi, float3 qlo, float
 // grows by at most the tree's depth, which stays below the margin.
 __device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes, int n_inner, int n_leaves,
                                               float3 qlo, float3 qhi, float ext2, int* stack, int& sp,
-                                              int* list, int nc, bool& overflow) {
+                                              int* list, int nc, bool& overflow, uint32_t& box_tests) {
     const int lane = threadIdx.x & 31;
     int guard = 0;
     while (sp > 0 && nc <= kListCap - 64) {
@@ -180,6 +180,7 @@ __device__ __forceinline__ int walk_and_stage(const BvhNode* __restrict__ nodes,
             break;
         }
         const int take = sp > kStackCapW - kNarrowMargin ? 1 : min(sp, 32);
+        box_tests += (uint32_t)(n_leaves > 1 ? 2 * take : take);
         int node = -1;
         if (lane < take) node = stack[sp - 1 - lane];
         sp -= take;
@@ -258,7 +259,36 @@ struct WarpSmemT {
     float4 tpln[32];                             // their planes
     uint16_t pairs[160];                         // (slot << 5) | chunk lane: (voxel, triangle) pairs to filter
     unsigned long long key[RaySlots<RPL>::kRays][32];  // closest hit: (t bits << 32) | (id << 1) | front
+    unsigned long long work[4];                  // node, reach, filter-pair and exact-test counts (lane 0 writes)
+    uint32_t near_edge;                          // exact-test hits within 1e-6 of an edge (lane 0 writes)
 };
+
+enum { kWorkNodes = 0, kWorkReach = 1, kWorkPairs = 2, kWorkExact = 3 };
+
+// Work counts of the warp (counting kernels only), kept in its shared state by lane 0
+// and added to the caller's counters once per warp (work_flush).
+template <int RPL>
+__device__ __forceinline__ void work_reset(WarpSmemT<RPL>& w) {
+    if ((threadIdx.x & 31) == 0) {
+        for (int i = 0; i < 4; ++i) w.work[i] = 0ull;
+        w.near_edge = 0u;
+    }
+    __syncwarp();
+}
+
+
+
+template <int RPL>
+__device__ __forceinline__ void work_flush(WarpSmemT<RPL>& w, rtsdf_counters* counters) {
+    __syncwarp();
+    if (counters && (threadIdx.x & 31) == 0) {
+        if (w.work[kWorkNodes]) atomicAdd(reinterpret_cast<unsigned long long*>(&counters->node_tests), w.work[kWorkNodes]);
+        if (w.work[kWorkReach]) atomicAdd(reinterpret_cast<unsigned long long*>(&counters->reach_tests), w.work[kWorkReach]);
+        if (w.work[kWorkPairs]) atomicAdd(reinterpret_cast<unsigned long long*>(&counters->filter_pairs), w.work[kWorkPairs]);
+        if (w.work[kWorkExact]) atomicAdd(reinterpret_cast<unsigned long long*>(&counters->exact_tests), w.work[kWorkExact]);
+        if (w.near_edge) atomicAdd(&counters->near_edge_hits, w.near_edge);
+    }
+}
 
 // Component comp of ray r's direction at a slot (one scalar shared-memory load).
 template <int RPL>
@@ -268,8 +298,8 @@ __device__ __forceinline__ float dq_comp(const WarpSmemT<RPL>& w, int comp, int 
 
 // Exact Moller-Trumbore test of one queued (voxel, ray, triangle) item; the
 // closest hit per ray (ties to the lower id) is kept with a 64-bit atomicMin.
-template <int RPL>
-__device__ __forceinline__ void run_item(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
+template <int RPL, bool kCount>
+__device__ __forceinline__ bool run_item(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, uint32_t item,
                                          float tmax) {
     constexpr int kB = RaySlots<RPL>::kRBits;
     const int c = (int)(item >> (5 + kB)), slot = (int)((item >> kB) & 31u), r = (int)(item & ((1u << kB) - 1u));
@@ -280,13 +310,41 @@ __device__ __forceinline__ void run_item(WarpSmemT<RPL>& w, const BvhLeaf* __res
     const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
     const float3 A = make_float3(v0.x, v0.y, v0.z);
     const float3 e1 = make_float3(e1f.x, e1f.y, e1f.z), e2 = make_float3(e2f.x, e2f.y, e2f.z);
-    float t;
+    float t, margin = 1.0f;
     bool front;
-    if (ray_tri(o, d, A, e1, e2, tmax, t, front)) {
+    const bool hit = kCount ? ray_tri(o, d, A, e1, e2, tmax, t, front, margin) : ray_tri(o, d, A, e1, e2, tmax, t, front);
+    if (hit) {
         const uint32_t id = (uint32_t)__float_as_int(v0.w);
         const unsigned long long key =
             ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)((id << 1) | (front ? 1u : 0u));
         atomicMin(&w.key[r][slot], key);
+    }
+    return hit && margin < 1e-6f;
+}
+
+// Work counts of one brick, the same in every lane (added to the warp's shared totals
+// once per brick, at the end of refine_brick).
+struct BrickWork {
+    uint32_t pairs = 0, exact = 0, near = 0;
+};
+
+// Lane 0 adds n to the warp's shared count i (outside the hot loops: once per BVH walk).
+template <int RPL>
+__device__ __forceinline__ void work_add(WarpSmemT<RPL>& w, int i, uint32_t n) {
+    if ((threadIdx.x & 31) == 0) w.work[i] += n;
+}
+
+// Exact tests of the items of the first n lanes (items[lane]); with kCount, counted.
+template <int RPL, bool kCount>
+__device__ __forceinline__ void run_items(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, const uint32_t* items,
+                                          int n, float tmax, BrickWork& bw) {
+    const int lane = threadIdx.x & 31;
+    if (kCount) {
+        const bool near = lane < n && run_item<RPL, true>(w, leaves, items[lane], tmax);
+        bw.exact += (uint32_t)n;
+        bw.near += (uint32_t)__popc(__ballot_sync(0xffffffffu, near));
+    } else if (lane < n) {
+        run_item<RPL, false>(w, leaves, items[lane], tmax);
     }
 }
 
@@ -338,13 +396,14 @@ __device__ __forceinline__ uint32_t filter_pair(const WarpSmemT<RPL>& w, int v, 
 }
 
 // Exact tests of full batches of 32 queued items.
-template <int RPL>
-__device__ __forceinline__ void run_full_batches(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, float tmax) {
+template <int RPL, bool kCount>
+__device__ __forceinline__ void run_full_batches(WarpSmemT<RPL>& w, const BvhLeaf* __restrict__ leaves, float tmax,
+                                                 BrickWork& bw) {
     const int lane = threadIdx.x & 31;
     int qn = w.qn;
     if (qn >= 32) {
         while (qn >= 32) {
-            run_item(w, leaves, w.queue[qn - 32 + lane], tmax);
+            run_items<RPL, kCount>(w, leaves, w.queue + (qn - 32), 32, tmax, bw);
             qn -= 32;
         }
         __syncwarp();
@@ -355,9 +414,11 @@ __device__ __forceinline__ void run_full_batches(WarpSmemT<RPL>& w, const BvhLea
 
 // Filters one (voxel slot, chunk triangle) pair per lane (lanes >= n idle) and queues
 // the surviving (voxel, ray, triangle) items.
-template <int RPL>
-__device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int base, int cb, float tmax) {
+template <int RPL, bool kCount>
+__device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int base, int cb, float tmax,
+                                                 BrickWork& bw) {
     const int lane = threadIdx.x & 31;
+    if (kCount) bw.pairs += (uint32_t)n;
     if (lane < n) {
         const uint32_t p = w.pairs[base + lane];
         const int v = (int)(p >> 5), j = (int)(p & 31u);
@@ -391,7 +452,7 @@ __device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int b
 // multiply-adds because they decide nothing the oracle decides.
 // RPL: rays per lane and group (2, 4 or 8); calls with R <= RPL rays per voxel run
 // one group, so small ray counts do not pay for eight.
-template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane>
+template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane, bool kCount = false>
 __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode* __restrict__ nodes,
                                              const BvhLeaf* __restrict__ leaves, int n_leaves, int n_inner,
                                              const int32_t* __restrict__ nearest,
@@ -417,8 +478,11 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
         sp0 = 1;
     }
     __syncwarp();
+    BrickWork bw;
+    uint32_t box_tests = 0;
     const int nc_all = walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack, sp0, w.list, 0,
-                                      overflow);
+                                      overflow, box_tests);
+    if (kCount) work_add(w, kWorkNodes, box_tests);
     const bool complete = sp0 == 0;
     for (int pass = 0; pass * 32 < nm; ++pass) {
         const int slot = pass * 32 + lane;
@@ -488,9 +552,15 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             bool first = true;
             while (first || sp > 0) {
                 first = false;
+                box_tests = 0;
                 const int nc = complete ? nc_all
                                         : walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack,
-                                                         sp, w.list, 0, overflow);
+                                                         sp, w.list, 0, overflow, box_tests);
+                // every (voxel, staged triangle) pair of the pass meets the reach test
+                if (kCount) {
+                    work_add(w, kWorkNodes, box_tests);
+                    work_add(w, kWorkReach, (uint32_t)(nv * nc));
+                }
                 if (lane == 0) w.qn = 0;
                 __syncwarp();
                 for (int cb = 0; cb < nc; cb += 32) {
@@ -530,19 +600,19 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                         while (np >= 32) {
                             __syncwarp();
                             np -= 32;
-                            filter_and_queue<RPL>(w, 32, np, cb, a.tmax);
-                            run_full_batches(w, leaves, a.tmax);
+                            filter_and_queue<RPL, kCount>(w, 32, np, cb, a.tmax, bw);
+                            run_full_batches<RPL, kCount>(w, leaves, a.tmax, bw);
                         }
                     }
                     __syncwarp();
                     if (np > 0) {
-                        filter_and_queue<RPL>(w, np, 0, cb, a.tmax);
-                        run_full_batches(w, leaves, a.tmax);
+                        filter_and_queue<RPL, kCount>(w, np, 0, cb, a.tmax, bw);
+                        run_full_batches<RPL, kCount>(w, leaves, a.tmax, bw);
                     }
                 }
                 {
                     const int qn = w.qn;
-                    if (lane < qn) run_item(w, leaves, w.queue[lane], a.tmax);
+                    run_items<RPL, kCount>(w, leaves, w.queue, qn, a.tmax, bw);
                     __syncwarp();
                 }
                 __syncwarp();
@@ -589,6 +659,11 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             sdf[lin] = neg ? -df : df;
         }
         __syncwarp();
+    }
+    if (kCount && lane == 0) {
+        w.work[kWorkPairs] += bw.pairs;
+        w.work[kWorkExact] += bw.exact;
+        w.near_edge += bw.near;
     }
     n_ovf += overflow ? 1u : 0u;
 }

@@ -199,7 +199,7 @@ __device__ __forceinline__ bool sphere_dir(uint32_t voxel, uint32_t ray, uint32_
 // Moller-Trumbore with precomputed edges e1 = B - A, e2 = C - A.  Hit iff
 // 0 < t <= tmax; front iff det > 0 (the ray meets the counter-clockwise side).
 __device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 A, float3 e1, float3 e2, float tmax,
-                                        float& t, bool& front) {
+                                        float& t, bool& front, float& margin) {
     const float3 p = cross3(d, e2);
     const float det = dot3(e1, p);
     if (det == 0.0f) return false;
@@ -209,12 +209,20 @@ __device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 A, float3 e1,
     if (u < 0.0f || u > 1.0f) return false;
     const float3 q = cross3(tv, e1);
     const float w = dot3(d, q) * inv;
-    if (w < 0.0f || u + w > 1.0f) return false;
+    const float uw = u + w;
+    if (w < 0.0f || uw > 1.0f) return false;
     const float tt = dot3(e2, q) * inv;
     if (!(tt > 0.0f && tt <= tmax)) return false;
     t = tt;
     front = det > 0.0f;
+    margin = fminf(fminf(u, w), 1.0f - uw);  // smallest barycentric coordinate of the hit
     return true;
+}
+
+__device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 A, float3 e1, float3 e2, float tmax,
+                                        float& t, bool& front) {
+    float margin;
+    return ray_tri(o, d, A, e1, e2, tmax, t, front, margin);
 }
 
 // ------------------------------------------------------------------ BVH layout

@@ -37,7 +37,7 @@ class RefineParams(C.Structure):
     _fields_ = [("mask_vox", C.c_float), ("rays_per_voxel", C.c_int32), ("max_ray_vox", C.c_float),
                 ("beta_vox", C.c_float), ("key", C.c_uint32 * 2), ("frame_index", C.c_uint32),
                 ("scene_id", C.c_uint32), ("accumulate", C.c_int32), ("sign_fallback", C.c_int32),
-                ("decay_alpha", C.c_float)]
+                ("decay_alpha", C.c_float), ("count_work", C.c_int32)]
 
 
 class ShadowParams(C.Structure):
@@ -50,10 +50,13 @@ class ShadowParams(C.Structure):
 class Counters(C.Structure):
     _fields_ = [("skipped_triangles", C.c_uint32), ("masked_voxels", C.c_uint32),
                 ("rays_hit", C.c_uint32), ("rays_failed", C.c_uint32),
-                ("stack_overflow", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("stack_overflow", C.c_uint32), ("near_edge_hits", C.c_uint32), ("reserved", C.c_uint32 * 2),
+                ("node_tests", C.c_uint64), ("reach_tests", C.c_uint64), ("filter_pairs", C.c_uint64),
+                ("exact_tests", C.c_uint64)]
 
 
 COUNTER_FIELDS = [f for f, _ in Counters._fields_ if f != "reserved"]
+COUNTER_WORDS = C.sizeof(Counters) // 4  # int32 words of a counters tensor
 
 BATCH_MAX_SCENES = 64
 BATCH_MAX_STEPS = 16
@@ -169,11 +172,11 @@ def make_grid(g) -> Grid:
     return Grid(int(g.nx), int(g.ny), int(g.nz), (C.c_float * 3)(*[float(v) for v in g.origin]), float(g.h))
 
 
-def make_refine_params(rp) -> RefineParams:
+def make_refine_params(rp, count_work: bool = False) -> RefineParams:
     return RefineParams(float(rp.mask_vox), int(rp.rays_per_voxel), float(rp.max_ray_vox), float(rp.beta_vox),
                         (C.c_uint32 * 2)(*[int(k) & 0xFFFFFFFF for k in rp.key]), int(rp.frame_index) & 0xFFFFFFFF,
                         int(rp.scene_id) & 0xFFFFFFFF, int(rp.accumulate), int(bool(rp.sign_fallback)),
-                        float(getattr(rp, "decay_alpha", 0.95)))
+                        float(getattr(rp, "decay_alpha", 0.95)), int(bool(count_work)))
 
 
 def make_shadow_params(sp) -> ShadowParams:
@@ -313,9 +316,14 @@ def rtsdf_kernel_launches() -> int:
     return int(lib().rtsdf_kernel_launches())
 
 
+def new_counters(device) -> torch.Tensor:
+    """A zeroed device counters block (rtsdf_counters) as int32 words."""
+    return torch.zeros(COUNTER_WORDS, dtype=torch.int32, device=device)
+
+
 def counters_dict(counters: torch.Tensor) -> dict:
-    vals = counters.cpu().tolist()
-    return {f: int(v) & 0xFFFFFFFF for f, v in zip(COUNTER_FIELDS, vals)}
+    raw = Counters.from_buffer_copy(counters.cpu().numpy().tobytes()[:C.sizeof(Counters)])
+    return {f: int(getattr(raw, f)) for f in COUNTER_FIELDS}
 
 
 # ------------------------------------------------------------ a frame pipeline
@@ -342,7 +350,7 @@ class Pipeline:
         self.front = torch.zeros(shp, **i32)
         self.back = torch.zeros(shp, **i32)
         self.sdf = torch.empty(shp, dtype=torch.float32, device=dev)
-        self.counters = torch.zeros(8, **i32)
+        self.counters = new_counters(dev)
         u8 = dict(dtype=torch.uint8, device=dev)
         self.ws_vox = torch.empty(rtsdf_voxelize_workspace(self.T, self.g), **u8)
         self.bvh = torch.empty(rtsdf_bvh_bytes(self.T), **u8)
@@ -605,7 +613,7 @@ class Batch:
         self.sdf = torch.empty(self.nvox, dtype=torch.float32, device=dev)
         self.bvh = torch.empty(max(256, int(L.rtsdf_batch_bvh_bytes(self.plan))), dtype=torch.uint8, device=dev)
         self.ws = torch.empty(int(L.rtsdf_batch_workspace(self.plan)), dtype=torch.uint8, device=dev)
-        self.counters = torch.zeros(8, **i32)
+        self.counters = new_counters(dev)
         self.buffers = BatchBuffers(self.verts.data_ptr(), self.tris.data_ptr(), self.seed.data_ptr(),
                                     self.buf_b.data_ptr(), self.rep_tri.data_ptr(), self.bvh.data_ptr(),
                                     self.bvh.numel(), self.dist_bits.data_ptr(), self.front.data_ptr(),

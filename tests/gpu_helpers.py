@@ -36,7 +36,7 @@ def gpu_rebuild(sc: scenes.Scene, frames: int | None = None, frame0: int = 0):
     for f in range(nf):
         rp = dataclasses.replace(sc.refine, frame_index=frame0 + f,
                                  accumulate=int(sc.refine.accumulate) if f > 0 else 0)
-        P.refine(verts, tris, rt.make_refine_params(rp))
+        P.refine(verts, tris, rt.make_refine_params(rp, count_work=True))
     torch.cuda.synchronize()
     out = dict(seed=seed, rep_tri=rep, nearest=nearest,
                dist_bits=P.dist_bits.cpu().numpy().view(np.uint32).copy(),
@@ -65,6 +65,10 @@ def compare_rebuild(ref: dict, got: dict, sdf_tol: float = 1e-5, voxels=None):
     if voxels is None:
         d = np.abs(got["sdf"].astype(np.float64) - ref["sdf"].astype(np.float64))
         assert d.max() <= sdf_tol, (d.max(), np.unravel_index(d.argmax(), d.shape))
+        # hits within 1e-6 of a triangle edge: the GPU tests only the triangles its filters
+        # keep, the oracle every triangle, and the counts agree
+        if "near_edge" in ref and "counters" in got:
+            assert got["counters"]["near_edge_hits"] == ref["near_edge"], (got["counters"], ref["near_edge"])
     else:
         d = np.abs(got["sdf"].ravel()[sel].astype(np.float64) - ref["sdf"].ravel()[sel].astype(np.float64))
         assert d.max() <= sdf_tol

@@ -239,3 +239,23 @@ def test_texture_entry_validation(lib):
     assert lib.rtsdf_shadow_tex(None, P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
     assert lib.rtsdf_texture_upload(None, P(FAKE), None) == 1
     lib.rtsdf_texture_destroy(None)
+
+
+def test_counters_layout_matches_the_header(tmp_path):
+    """The binding's rtsdf_counters mirrors the C struct: size and field offsets as a
+    C compiler lays out include/rtsdf.h."""
+    import subprocess
+    from paper_2210_06160_gb300 import rtsdf
+    src = tmp_path / "layout.c"
+    fields = [f for f, _ in rtsdf.Counters._fields_]
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rtsdf.h"\nint main(void) {\n'
+                   '    printf("%zu", sizeof(rtsdf_counters));\n'
+                   + "".join(f'    printf(" %zu", offsetof(rtsdf_counters, {f}));\n' for f in fields)
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
+                           str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(rtsdf.Counters)] + [getattr(rtsdf.Counters, f).offset for f in fields]
+    assert got == want
+    assert got[0] == 64 and rtsdf.COUNTER_WORDS == 16

@@ -96,3 +96,34 @@ def test_dynamic_room_full_size_sampled():
     for name, want in (("dist_bits", d), ("front", fr), ("back", bk)):
         np.testing.assert_array_equal(got[name].ravel()[sample], want[sample], err_msg=name)
     np.testing.assert_array_equal(got["dist_bits"].ravel()[~mask.ravel()], d[~mask.ravel()])
+
+
+def test_ghosting_matches_the_oracle():
+    """The Eq. (1) decay over the small animated room (5-frame stride): the GPU's
+    refined distances at the sampled masked voxels equal the oracle's bit for bit, so
+    the ghost fraction against the FP64 truth is the same on both sides."""
+    import bench
+    from tests import test_ghosting as tg
+    anim = tg._anim()
+    sc, g = anim.scene, anim.scene.grid
+    vv0 = oracle.to_voxel(scenes.room_frame(anim, tg.FRAMES[0]), g)
+    seed, rep, _ = oracle.voxelize(vv0, sc.tris, g)
+    near = oracle.jfa(g, seed, sc.jfa_steps)
+    _, mask = oracle.resolve(g, vv0, sc.tris, near, rep, sc.refine.mask_vox)
+    voxels = np.sort(np.random.default_rng(5).choice(np.flatnonzero(mask.ravel()), 1000, replace=False))
+    seq = tg._oracle_sequence(oracle, anim, 2, tg.FRAMES, voxels)
+    want, _ = tg._fractions(g, sc.tris, seq, voxels, sc.refine.mask_vox + 1.0)
+    P = rt.Pipeline(g, len(sc.verts), len(sc.tris))
+    tris = to_dev(sc.tris)
+    got_seq = []
+    for n, f in enumerate(tg.FRAMES):
+        verts = scenes.room_frame(anim, f)
+        rp = dataclasses.replace(sc.refine, frame_index=f, accumulate=2 if n > 0 else 0, decay_alpha=0.95)
+        P.rebuild(to_dev(verts), tris, sc.jfa_steps, rt.make_refine_params(rp))
+        torch.cuda.synchronize()
+        d = P.dist_bits.cpu().numpy().view(np.uint32).ravel().view(np.float32).copy()
+        got_seq.append((verts, seq[n][1], d))
+        sel = np.asarray([v for v in voxels if seq[n][1][v]])
+        np.testing.assert_array_equal(d[sel].view(np.uint32), seq[n][2][sel].view(np.uint32), err_msg=f"frame {f}")
+    got, _ = tg._fractions(g, sc.tris, got_seq, voxels, sc.refine.mask_vox + 1.0)
+    assert got == want and max(got) > 0.0

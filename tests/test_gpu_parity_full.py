@@ -3,9 +3,10 @@ benchmark times (the same Pipeline, the same per-frame parameters).
 
 Whole-grid comparisons where the oracle finishes in seconds (seeds,
 representative triangles, flooded seeds, the unmasked part of the field);
-sampled masked voxels for ray sampling (the oracle is brute force over all
-~109k triangles per ray); sampled receivers for the shadow, both sides marching
-the same oracle-built field.
+8,192 sampled masked voxels for ray sampling over two accumulated frames (the
+oracle is brute force over all ~109k triangles per ray); sampled receivers for the
+shadow, both sides marching the same field: the oracle-built coarse field, and the
+field the GPU refined.
 """
 import dataclasses
 
@@ -21,7 +22,7 @@ from tests.gpu_helpers import gpu_shadow, require_gpu, to_dev
 pytestmark = pytest.mark.gpu
 
 FRAMES = 2
-N_SAMPLE_VOXELS = 96
+N_SAMPLE_VOXELS = 8192
 N_SAMPLE_PIXELS = 20000
 
 
@@ -84,6 +85,7 @@ def test_room_unmasked_field_and_mask(room):
     assert got["counters"]["rays_failed"] == 0 and got["counters"]["stack_overflow"] == 0
 
 
+@pytest.mark.slow
 def test_room_sampled_refinement_bit_exact(room):
     _, got, ref = room
     s = ref["sample"]
@@ -104,3 +106,17 @@ def test_room_shadow_sampled_pixels(room):
     got = gpu_shadow(sc.grid, field, pos, nrm, sc.shadow)
     assert np.abs(got - want).max() <= 1e-4
     assert 0.0 < want.mean() < 1.0
+
+
+def test_room_shadow_on_the_refined_field(room):
+    """The 1920x1080 receivers' raymarch over the field the GPU refined (two frames of
+    8 rays): both sides march that same field."""
+    sc, got, _ = room
+    field = got["sdf"].astype(np.float32)
+    rng = np.random.default_rng(8)
+    pick = rng.choice(len(sc.recv_pos), N_SAMPLE_PIXELS, replace=False)
+    pos, nrm = sc.recv_pos[pick], sc.recv_nrm[pick]
+    want = oracle.shadow(sc.grid, field, pos, nrm, sc.shadow)
+    got_vis = gpu_shadow(sc.grid, field, pos, nrm, sc.shadow)
+    assert np.abs(got_vis - want).max() <= 1e-4
+    assert 0.0 < want.mean() < 1.0 and (want < 0.5).mean() > 0.01

@@ -229,8 +229,10 @@ def test_ray_triangle_against_plane_intersection(orc):
         if abs(margin) < 1e-4 or abs(t) < 1e-4 or abs(t - tmax) < 1e-4:
             continue
         want = margin > 0 and 0 < t <= tmax
-        hit, tt, front = orc.ray_tri(o, d, a, b, c, tmax)
+        hit, tt, front, m32 = orc.ray_tri(o, d, a, b, c, tmax, with_margin=True)
         assert hit == want
+        if hit:  # the smallest barycentric coordinate, as FP64 solves it
+            assert abs(m32 - margin) <= 1e-4 * max(1.0, abs(margin)) + 1e-5
         n_cmp += 1
         if hit:
             n_hit += 1
@@ -836,3 +838,41 @@ def test_fine_representative_triangles_two_resolutions(orc):
         qx, qy, qz = s & 1023, (s >> 10) & 1023, s >> 20
         a, b, c = (vc[T[t][n]] for n in range(3))
         assert orc.tri_box_overlap(a, b, c, (qx + 0.5, qy + 0.5, qz + 0.5), 0.5)
+
+
+def test_near_edge_hits_are_counted(orc):
+    """Exactness reading (hits within 1e-6 of a triangle edge are counted and
+    reported): rays aimed at points whose smallest barycentric coordinate is 3e-7 are
+    near-edge hits, at 1e-4 they are not; the brute-force refinement's count equals
+    the per-(ray, triangle) count of the same test."""
+    a = np.array([0.0, 0.0, 0.0]); b = np.array([4.0, 0.0, 0.0]); c = np.array([0.0, 4.0, 0.0])
+    d = np.array([0.0, 0.0, -1.0], np.float32)
+    for (u, w, near) in [(0.25, 0.25, False), (3e-7, 0.4, True), (0.4, 3e-7, True), (0.5, 0.5 - 3e-7, True),
+                         (1e-4, 0.3, False), (0.3, 1.0 - 0.3 - 1e-4, False)]:
+        p = a + u * (b - a) + w * (c - a)
+        o = (p + np.array([0.0, 0.0, 2.0])).astype(np.float32)
+        hit, t, front, m = orc.ray_tri(o, d, a, b, c, 8.0, with_margin=True)
+        assert hit and abs(t - 2.0) < 1e-6
+        assert (m < 1e-6) == near, (u, w, m)
+    # a tiny scene: the count of refine_voxels equals the count over every ray and triangle
+    V, T = scenes.icosphere(1)
+    V = (V * 3.0 + 5.0).astype(np.float32)
+    g = scenes.Grid(10, 10, 10, (0.0, 0.0, 0.0), 1.0)
+    rp = scenes.RefineParams(rays_per_voxel=16, max_ray_vox=8.0, key=(3, 9))
+    vox = np.arange(0, g.nvox, 11, dtype=np.int32)
+    dist = np.full(g.nvox, np.float32(100.0)).view(np.uint32)
+    fr, bk = np.zeros(g.nvox, np.uint32), np.zeros(g.nvox, np.uint32)
+    near = np.zeros(1, np.int64)
+    orc.refine_voxels(g, V, T, vox, rp, 0, dist, fr, bk, near_edge=near)
+    want = 0
+    for lin in vox:
+        i, j, k = lin % 10, (lin // 10) % 10, lin // 100
+        o = np.array([i + 0.5, j + 0.5, k + 0.5], np.float32)
+        for r in range(rp.rays_per_voxel):
+            dr, att = orc.sphere_dir(int(lin), r, 0, rp.key)
+            if att < 0:
+                continue
+            for tri in T:
+                hit, _, _, m = orc.ray_tri(o, dr, *V[tri], rp.max_ray_vox, with_margin=True)
+                want += bool(hit and m < 1e-6)
+    assert near[0] == want
