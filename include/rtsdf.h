@@ -268,6 +268,19 @@ rtsdf_status rtsdf_refine_2res(const rtsdf_grid* fine, const rtsdf_grid* coarse,
 rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm,
                           int32_t P, const rtsdf_shadow_params* p, float* vis, rtsdf_stream stream);
 
+/* rtsdf_shadow with the receivers regrouped for SIMT coherence (the same vis bit for
+ * bit: each receiver's march is independent of the others).  steps (P bytes of device
+ * memory, caller-owned, kept from call to call for the same receivers; zeroes the
+ * first time) holds each receiver's march length from the previous call: the step at
+ * which its march stopped, at most 255.  Within each block of 512 consecutive
+ * receivers the threads take the receivers in order of those lengths, so the lanes
+ * of a warp march about as long; every receiver's new length is written back.  Any
+ * contents of steps give the same vis; only the speed depends on them.  EINVAL as
+ * rtsdf_shadow, or when steps is NULL with P > 0. */
+rtsdf_status rtsdf_shadow_coherent(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm,
+                                   int32_t P, const rtsdf_shadow_params* p, float* vis, uint8_t* steps,
+                                   rtsdf_stream stream);
+
 /* ---------------------------------------------------------------- shadow, texture path */
 
 /* The shadow raymarch sampling the field through a 3D texture with hardware

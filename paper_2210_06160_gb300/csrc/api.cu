@@ -188,6 +188,15 @@ rtsdf_status rtsdf_shadow(const rtsdf_grid* g, const float* sdf, const float* po
     return shadow(*g, sdf, pos, nrm, P, *p, vis, cs(stream));
 }
 
+rtsdf_status rtsdf_shadow_coherent(const rtsdf_grid* g, const float* sdf, const float* pos, const float* nrm,
+                                   int32_t P, const rtsdf_shadow_params* p, float* vis, uint8_t* steps,
+                                   rtsdf_stream stream) {
+    if (!grid_ok(g) || !p || P < 0 || !buf_ok(sdf, 16)) return RTSDF_EINVAL;
+    if (P > 0 && (!buf_ok(pos, 4) || !buf_ok(nrm, 4) || !buf_ok(vis, 4) || !steps)) return RTSDF_EINVAL;
+    if (!shadow_params_ok(p)) return RTSDF_EINVAL;
+    return shadow_coherent(*g, sdf, pos, nrm, P, *p, vis, steps, cs(stream));
+}
+
 rtsdf_status rtsdf_sample(const rtsdf_grid* g, const float* sdf, const float* pts, int32_t M, float* out,
                           rtsdf_stream stream) {
     if (!grid_ok(g) || M < 0 || !buf_ok(sdf, 16)) return RTSDF_EINVAL;

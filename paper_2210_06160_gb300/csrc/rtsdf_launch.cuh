@@ -70,6 +70,8 @@ rtsdf_status refine(const rtsdf_grid& g, int32_t T, const void* bvh, const int32
 
 rtsdf_status shadow(const rtsdf_grid& g, const float* sdf, const float* pos, const float* nrm, int32_t P,
                     const rtsdf_shadow_params& p, float* vis, cudaStream_t s);
+rtsdf_status shadow_coherent(const rtsdf_grid& g, const float* sdf, const float* pos, const float* nrm, int32_t P,
+                             const rtsdf_shadow_params& p, float* vis, uint8_t* steps, cudaStream_t s);
 
 rtsdf_status sample(const rtsdf_grid& g, const float* sdf, const float* pts, int32_t M, float* out, cudaStream_t s);
 

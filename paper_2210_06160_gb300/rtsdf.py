@@ -104,6 +104,8 @@ _SIGS = {
     "rtsdf_refine_2res": (C.c_int, [C.POINTER(Grid), C.POINTER(Grid), _P, C.c_int32, _P, C.c_int32, _P, C.c_size_t,
                                     _P, _P, C.POINTER(RefineParams), _P, _P, _P, _P, _P, C.c_size_t, _P, _P]),
     "rtsdf_shadow": (C.c_int, [C.POINTER(Grid), _P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P]),
+    "rtsdf_shadow_coherent": (C.c_int, [C.POINTER(Grid), _P, _P, _P, C.c_int32, C.POINTER(ShadowParams), _P, _P,
+                                        _P]),
     "rtsdf_sample": (C.c_int, [C.POINTER(Grid), _P, _P, C.c_int32, _P, _P]),
     "rtsdf_texture_create": (C.c_int, [C.POINTER(Grid), C.POINTER(C.c_void_p)]),
     "rtsdf_texture_destroy": (None, [_P]),
@@ -312,6 +314,13 @@ def rtsdf_shadow(grid: Grid, sdf, pos, nrm, params: ShadowParams, vis, stream=No
                               _dev(vis, torch.float32, "vis"), _stream(stream)), "rtsdf_shadow")
 
 
+def rtsdf_shadow_coherent(grid: Grid, sdf, pos, nrm, params: ShadowParams, vis, steps, stream=None) -> None:
+    _check(lib().rtsdf_shadow_coherent(C.byref(grid), _dev(sdf, torch.float32, "sdf"),
+                                       _dev(pos, torch.float32, "pos"), _dev(nrm, torch.float32, "nrm"),
+                                       pos.shape[0], C.byref(params), _dev(vis, torch.float32, "vis"),
+                                       _dev(steps, torch.uint8, "steps"), _stream(stream)), "rtsdf_shadow_coherent")
+
+
 def rtsdf_kernel_launches() -> int:
     return int(lib().rtsdf_kernel_launches())
 
@@ -412,10 +421,18 @@ class Pipeline:
             self._side = torch.cuda.Stream(device=self.bvh.device)
         return self._side
 
-    def shadow(self, pos, nrm, params: ShadowParams, vis=None, stream=None):
+    def shadow(self, pos, nrm, params: ShadowParams, vis=None, stream=None, coherent: bool = True):
+        """The raymarch of every receiver; `coherent` regroups the receivers by the
+        march lengths of this pipeline's previous call (same results, fewer idle lanes)."""
         if vis is None:
             vis = torch.empty(pos.shape[0], dtype=torch.float32, device=pos.device)
-        rtsdf_shadow(self.g, self.sdf, pos, nrm, params, vis, stream)
+        if coherent:
+            steps = getattr(self, "_march_steps", None)
+            if steps is None or steps.numel() != pos.shape[0] or steps.device != pos.device:
+                steps = self._march_steps = torch.zeros(pos.shape[0], dtype=torch.uint8, device=pos.device)
+            rtsdf_shadow_coherent(self.g, self.sdf, pos, nrm, params, vis, steps, stream)
+        else:
+            rtsdf_shadow(self.g, self.sdf, pos, nrm, params, vis, stream)
         return vis
 
     def sample(self, pts, out=None, stream=None):

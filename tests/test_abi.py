@@ -114,6 +114,12 @@ def test_refine_and_shadow_parameter_validation(lib):
     assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
     sp = ShadowParams((C.c_float * 3)(0, 1, 0), 8.0, 10, 0.0)
     assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), None) == 1
+    # the regrouped march: the same checks, and its march-length buffer must be given
+    ok = ShadowParams((C.c_float * 3)(0, 1, 0), 8.0, 10, 1.0)
+    assert lib.rtsdf_shadow_coherent(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(sp), P(FAKE), P(FAKE),
+                                     None) == 1
+    assert lib.rtsdf_shadow_coherent(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(ok), P(FAKE), None,
+                                     None) == 1
 
 
 def test_adjoint_entry_validation(lib):

@@ -254,6 +254,38 @@ def test_shadow_parity_on_analytic_field():
         assert np.abs(got - want).max() <= SHADOW_TOL
 
 
+def test_coherent_shadow_equals_plain_shadow():
+    """The regrouped raymarch gives the plain raymarch's visibilities bit for bit,
+    whatever the march lengths it regroups by (zeroes, the previous call's, random
+    bytes), on receiver counts below, at and above the 512-receiver block; and the
+    lengths it writes are the plain march's stopping steps."""
+    g = scenes.Grid(50, 40, 30, (0.0, 0.0, 0.0), 0.04)
+    k, j, i = np.meshgrid(*(np.arange(n) + 0.5 for n in (30, 40, 50)), indexing="ij")
+    f = np.minimum(np.sqrt((i - 25) ** 2 + (j - 25) ** 2 + (k - 15) ** 2) - 7.0, j - 3.0).astype(np.float32)
+    rng = np.random.default_rng(9)
+    sp = scenes.ShadowParams(light_dir=(0.3, 1.0, 0.2), k=8.0, steps=96, max_step_vox=1.25, jitter_vox=0.5,
+                             frame_index=3)
+    for P in (1, 300, 512, 5000, 12345):
+        pos = np.stack([rng.uniform(0, 2.0, P), np.full(P, 0.13), rng.uniform(0, 1.2, P)], 1).astype(np.float32)
+        nrm = np.tile(np.array([[0.0, 1.0, 0.0]], np.float32), (P, 1))
+        want = oracle.shadow(g, f, pos, nrm, sp)
+        plain = gpu_shadow(g, f, pos, nrm, sp)
+        dpos, dnrm, dsdf = to_dev(pos), to_dev(nrm), to_dev(f)
+        steps = torch.zeros(P, dtype=torch.uint8, device="cuda")
+        vis = torch.empty(P, dtype=torch.float32, device="cuda")
+        gg, spp = rt.make_grid(g), rt.make_shadow_params(sp)
+        for init in ("zeros", "previous", "random"):
+            if init == "random":
+                steps.copy_(torch.from_numpy(rng.integers(0, 256, P).astype(np.uint8)))
+            rt.rtsdf_shadow_coherent(gg, dsdf, dpos, dnrm, spp, vis, steps)
+            np.testing.assert_array_equal(vis.cpu().numpy(), plain, err_msg=f"P={P} {init}")
+        assert np.abs(plain - want).max() <= SHADOW_TOL
+        st = steps.cpu().numpy().astype(int)
+        assert st.max() <= sp.steps and st.max() > 0
+        if P >= 5000:
+            assert len(np.unique(st)) > 5  # marches of many lengths were regrouped
+
+
 def test_accumulation_is_monotone_and_resumable():
     """Frames 0..3 in one run equal frames 0..1 then 2..3 resumed from the saved
     state (counter-based directions make the state a complete checkpoint)."""
