@@ -171,8 +171,9 @@ rtsdf_status rtsdf_build_bvh(const float* verts, int32_t V, const int32_t* tris,
  * output BVH buffer; arguments, outputs and errors are those of rtsdf_build_bvh, and
  * T > RTSDF_NOALLOC_MAX_TRIS returns RTSDF_ENOMEM.
  * The first call on a device looks up the array's device address (one-time set-up
- * per device, with that device current); make that first call before any stream
- * capture.  Every call on a device uses the same array, which keeps the previous
+ * per device, with that device current; looked up again if the device's context
+ * has changed since, e.g. after cudaDeviceReset); make that first call before any
+ * stream capture.  Every call on a device uses the same array, which keeps the previous
  * call's contents (the build clears what must start at zero): calls that can
  * overlap on the GPU (other streams, other host threads) race, so the caller must
  * serialise them. */

@@ -21,21 +21,59 @@ static __device__ __align__(256) unsigned char g_bvh_scratch[RTSDF_NOALLOC_SCRAT
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+    void* ptr = nullptr;
+    unsigned long long ctx = 0;  // id of the context the address belongs to
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the scratch array on the current device.  Host code only
-// sees a host-side stand-in under the array's name, so the address must be
-// queried once per device, with that device current.
+// Id of the calling thread's current CUDA context (0 when there is none or the
+// driver cannot tell), through the driver's cuCtxGetCurrent and cuCtxGetId, found
+// at run time so that the library needs no link against the driver.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(a);
+            get_id = reinterpret_cast<GetId>(b);
+        }
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || ctx == nullptr || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current device's context.  Host code
+// only sees a host-side stand-in under the array's name, so the address is looked
+// up with the device current: once per device, and again whenever that device's
+// context has changed since (a cudaDeviceReset makes a new context, into which the
+// module, and so the array, is loaded anew).
 rtsdf_status scratch_on_current_device(void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RTSDF_ECUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_scratch_ptr[dev] == nullptr) {
+    const unsigned long long ctx = current_context_id();
+    ScratchAddr& c = g_scratch[dev];
+    if (c.ptr == nullptr || ctx == 0 || c.ctx != ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_bvh_scratch) != cudaSuccess || p == nullptr) return RTSDF_ECUDA;
-        g_scratch_ptr[dev] = p;
+        c.ptr = p;
+        c.ctx = current_context_id();  // the lookup made the context current if there was none
     }
-    *out = g_scratch_ptr[dev];
+    *out = c.ptr;
     return RTSDF_OK;
 }
 
