@@ -94,8 +94,9 @@ __device__ __forceinline__ void jfa_column_generic(const uint32_t* __restrict__ 
 // (two lanes per instruction).
 //
 // The argmin of a group of candidates that share an output (the taps of one plane)
-// takes two phases, each a tree of 3-input minima (one DPX instruction): H = the
-// minimum of the distance bits (non-negative floats order like their bits), then
+// takes two phases, each a tree of unsigned minima (__vimin3_u32; on sm_103a each
+// lowers to two 2-input minima, measured): H = the minimum of the distance bits
+// (non-negative floats order like their bits), then
 // L = the minimum of bits(2 (d - H)) + s, which is s for the candidates at
 // distance H and at least 2^30 (above every packed seed, 1022 << 20 | ...) for the
 // others; where s is the empty marker the sum wraps to at least 2^30 - 1, still above

@@ -10,6 +10,9 @@ launch ends quickly while the kernel sees the benchmark's voxel size and scene.
     python -m paper_2210_06160_gb300.profile_cases shadow
         the 1920x1080 shadow raymarch of the room on its rebuilt 400x200x400
         field (only the field and the receivers stay resident)
+    python -m paper_2210_06160_gb300.profile_cases shadow-coherent
+        the same with rtsdf_shadow_coherent: three calls, the second and third
+        regrouped by the march lengths of the call before
     python -m paper_2210_06160_gb300.profile_cases adjoint
         the 128^3 differentiation workload: one tracked forward, then three
         rtsdf_backward calls (65,536 samples, 512x512 shadow image)
@@ -56,7 +59,7 @@ def case_refine_subbox(frames: int = 3) -> None:
     print("refine-subbox ok", rt.counters_dict(P.counters))
 
 
-def case_shadow() -> None:
+def case_shadow(coherent: bool = False) -> None:
     sc = scenes.scene_room()
     v, t = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda()
     P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris))
@@ -70,8 +73,13 @@ def case_shadow() -> None:
     pos, nrm = torch.from_numpy(sc.recv_pos).cuda(), torch.from_numpy(sc.recv_nrm).cuda()
     vis = torch.empty(len(sc.recv_pos), dtype=torch.float32, device="cuda")
     g, sp = rt.make_grid(sc.grid), rt.make_shadow_params(sc.shadow)
-    for _ in range(3):
-        rt.rtsdf_shadow(g, sdf, pos, nrm, sp, vis)
+    if coherent:
+        steps = torch.zeros(len(sc.recv_pos), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            rt.rtsdf_shadow_coherent(g, sdf, pos, nrm, sp, vis, steps)
+    else:
+        for _ in range(3):
+            rt.rtsdf_shadow(g, sdf, pos, nrm, sp, vis)
     torch.cuda.synchronize()
     print("shadow ok", float(vis.mean()))
 
@@ -112,6 +120,8 @@ if __name__ == "__main__":
         case_jfa()
     elif which == "shadow":
         case_shadow()
+    elif which == "shadow-coherent":
+        case_shadow(coherent=True)
     elif which == "adjoint":
         case_adjoint()
     elif which == "batch":
