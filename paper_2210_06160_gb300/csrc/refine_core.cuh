@@ -348,16 +348,30 @@ __device__ __forceinline__ void run_items(WarpSmemT<RPL>& w, const BvhLeaf* __re
     }
 }
 
-// Which rays of one (voxel slot v, staged triangle) pair can hit the triangle: each
-// ray's line must pass within rho of the triangle's bounding sphere centre with the
-// centre at most rho behind the origin (off the rho-sphere by more than rho*sqrt(2)
-// that is exactly tc >= sqrt(dd - rho^2); nearer, tc >= -rho is kept, a superset);
-// and the ray must cross the triangle's plane at a parameter t_p = sd / dn in
-// [0, tmax], written without a division as |sd - h dn| <= h |dn| (h = tmax / 2) and
-// widened by eps in sd.  All margins exceed the FP32 rounding of both sides, so no
-// triangle the exact test accepts is dropped.
+// Which rays of one (voxel slot v, staged triangle) pair can hit the triangle.  Two
+// necessary conditions, each a dot product of the ray direction d with a per-pair
+// vector against a per-pair threshold:
+//  - the line of the ray passes within rho of the triangle's bounding sphere centre
+//    c, with the centre at most rho behind the origin: tc = (c - o).d >= thr, where
+//    off the rho-sphere by more than rho*sqrt(2) thr = sqrt(|c - o|^2 - rho^2) is the
+//    exact cone, and nearer thr = -rho (every point of the sphere at t >= 0 has
+//    tc >= t - rho >= -rho);
+//  - the ray crosses the triangle's plane at t_p = sd / dn in [0, tmax] (sd the
+//    signed distance of the plane from the origin, dn = n.d).  That holds exactly
+//    when sd*dn >= sd^2 / tmax (the parabola f(sd) = sd*dn - sd^2/tmax is
+//    non-negative between its roots 0 and tmax*dn), so with m = sd*n the test is
+//    m.d >= sd^2/tmax - M.  The margin M = 1.5 eps + eps^2/tmax covers every sd in
+//    [-eps, tmax*dn + eps], the plane crossing widened by eps in sd (where f >=
+//    -(eps |dn| + eps^2/tmax)), with eps/2 to spare for rounding.
+// Each threshold is folded into the first FMA of its dot product, so a ray passes
+// when both results are non-negative: the OR of their bit patterns has a clear sign
+// bit, and a funnel shift appends that bit to the pair's mask.  All margins exceed
+// the FP32 rounding of both sides (values of at most a few tens of voxels; 1e-4
+// absolute and 1e-6 relative in the cone, eps >= 2e-3 in the plane), so no triangle
+// the exact test accepts is dropped.
 template <int RPL>
-__device__ __forceinline__ uint32_t filter_pair(const WarpSmemT<RPL>& w, int v, int j, float tmax) {
+__device__ __forceinline__ uint32_t filter_pair(const WarpSmemT<RPL>& w, int v, int j, float tmax, float inv_tmax) {
+    constexpr int kQ = (RPL + 3) / 4;
     const float4 o = w.origin[v];
     const float4 sph = w.tsph[j], pl = w.tpln[j];
     const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
@@ -367,32 +381,32 @@ __device__ __forceinline__ uint32_t filter_pair(const WarpSmemT<RPL>& w, int v, 
     // v * rsqrt(v) is within a few ulp of sqrt(v) (a few 1e-7 relative), well inside the
     // 1e-6 relative and 1e-4 absolute margins, so the threshold stays below the exact one
     const float v2 = dd - rho2;
-    const float thr = dd > 2.0f * rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho;
+    const float thr = dd > 2.0f * rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho * 1.000001f - 1e-4f;
     const float sd = pl.w - __fmaf_rn(pl.x, o.x, __fmaf_rn(pl.y, o.y, pl.z * o.z));
     const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
-    const float h = 0.5f * tmax;
+    const float marg = __fmaf_rn(eps * eps, inv_tmax, 1.5f * eps);
+    const float bq = __fmaf_rn(sd * inv_tmax, sd, -marg);
     const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
-    const float2 nx2 = make_float2(pl.x, pl.x), ny2 = make_float2(pl.y, pl.y), nz2 = make_float2(pl.z, pl.z);
-    const float2 sd2 = make_float2(sd, sd), mh2 = make_float2(-h, -h);
-    uint32_t pm = 0;
+    const float2 mx2 = make_float2(sd * pl.x, sd * pl.x), my2 = make_float2(sd * pl.y, sd * pl.y),
+                 mz2 = make_float2(sd * pl.z, sd * pl.z);
+    const float2 nthr2 = make_float2(-thr, -thr), nbq2 = make_float2(-bq, -bq);
+    uint32_t fail = 0;  // bit r set: ray r fails one of the tests
 #pragma unroll
-    for (int q = 0; q < (RPL + 3) / 4; ++q) {
+    for (int q = kQ - 1; q >= 0; --q) {
         const float4 qx = w.dq[0][q][v], qy = w.dq[1][q][v], qz = w.dq[2][q][v];
         const float2 xs[2] = {make_float2(qx.x, qx.y), make_float2(qx.z, qx.w)};
         const float2 ys[2] = {make_float2(qy.x, qy.y), make_float2(qy.z, qy.w)};
         const float2 zs[2] = {make_float2(qz.x, qz.y), make_float2(qz.z, qz.w)};
 #pragma unroll
-        for (int hq = 0; hq < (RPL >= 4 ? 2 : 1); ++hq) {
-            const int r = 4 * q + 2 * hq;
-            const float2 tc = __ffma2_rn(cx2, xs[hq], __ffma2_rn(cy2, ys[hq], __fmul2_rn(cz2, zs[hq])));
-            const float2 dn = __ffma2_rn(nx2, xs[hq], __ffma2_rn(ny2, ys[hq], __fmul2_rn(nz2, zs[hq])));
-            const float2 u = __ffma2_rn(mh2, dn, sd2);  // sd - h dn
-            const bool ok0 = tc.x >= thr && fabsf(u.x) <= __fmaf_rn(h, fabsf(dn.x), eps);
-            const bool ok1 = tc.y >= thr && fabsf(u.y) <= __fmaf_rn(h, fabsf(dn.y), eps);
-            pm |= ((ok0 ? 1u : 0u) << r) | ((ok1 ? 1u : 0u) << (r + 1));
+        for (int hq = (RPL >= 4 ? 1 : 0); hq >= 0; --hq) {
+            const float2 tc = __ffma2_rn(cx2, xs[hq], __ffma2_rn(cy2, ys[hq], __ffma2_rn(cz2, zs[hq], nthr2)));
+            const float2 pp = __ffma2_rn(mx2, xs[hq], __ffma2_rn(my2, ys[hq], __ffma2_rn(mz2, zs[hq], nbq2)));
+            // rays are appended from the highest index down, so ray r ends at bit r
+            fail = __funnelshift_l(__float_as_uint(tc.y) | __float_as_uint(pp.y), fail, 1);
+            fail = __funnelshift_l(__float_as_uint(tc.x) | __float_as_uint(pp.x), fail, 1);
         }
     }
-    return pm & w.okm[v];
+    return ~fail & w.okm[v];
 }
 
 // Exact tests of full batches of 32 queued items.
@@ -416,13 +430,13 @@ __device__ __forceinline__ void run_full_batches(WarpSmemT<RPL>& w, const BvhLea
 // the surviving (voxel, ray, triangle) items.
 template <int RPL, bool kCount>
 __device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int base, int cb, float tmax,
-                                                 BrickWork& bw) {
+                                                 float inv_tmax, BrickWork& bw) {
     const int lane = threadIdx.x & 31;
     if (kCount) bw.pairs += (uint32_t)n;
     if (lane < n) {
         const uint32_t p = w.pairs[base + lane];
         const int v = (int)(p >> 5), j = (int)(p & 31u);
-        uint32_t pm = filter_pair<RPL>(w, v, j, tmax);
+        uint32_t pm = filter_pair<RPL>(w, v, j, tmax, inv_tmax);
         if (pm) {
             int pos = atomicAdd(&w.qn, __popc(pm));
             while (pm) {
@@ -464,6 +478,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                                              uint32_t& n_fail, uint32_t& n_ovf) {
     const int lane = threadIdx.x & 31;
     const float ext = a.tmax * 1.00001f + 1e-3f;
+    const float inv_tmax = 1.0f / a.tmax;
     const int nm = __popcll(m);
     // every ray of the brick stays inside its voxel centres' box grown by the ray length
     const float3 qlo = make_float3((float)(bx * BX) + 0.5f, (float)(by * BY) + 0.5f, (float)(bz * BZ) + 0.5f);
@@ -600,13 +615,13 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                         while (np >= 32) {
                             __syncwarp();
                             np -= 32;
-                            filter_and_queue<RPL, kCount>(w, 32, np, cb, a.tmax, bw);
+                            filter_and_queue<RPL, kCount>(w, 32, np, cb, a.tmax, inv_tmax, bw);
                             run_full_batches<RPL, kCount>(w, leaves, a.tmax, bw);
                         }
                     }
                     __syncwarp();
                     if (np > 0) {
-                        filter_and_queue<RPL, kCount>(w, np, 0, cb, a.tmax, bw);
+                        filter_and_queue<RPL, kCount>(w, np, 0, cb, a.tmax, inv_tmax, bw);
                         run_full_batches<RPL, kCount>(w, leaves, a.tmax, bw);
                     }
                 }
