@@ -6,7 +6,8 @@ launch ends quickly while the kernel sees the benchmark's voxel size and scene.
         two 128 MB flooding buffers stay resident)
     python -m paper_2210_06160_gb300.profile_cases refine-subbox [frames]
         the room's refinement on a 200^3 sub-box at the benchmark's voxel size
-        (same triangles and brick statistics, ~8 M voxels)
+        (same triangles and brick statistics, ~8 M voxels); a last frame counts
+        the refinement's work units
     python -m paper_2210_06160_gb300.profile_cases shadow
         the 1920x1080 shadow raymarch of the room on its rebuilt 400x200x400
         field (only the field and the receivers stay resident)
@@ -56,7 +57,14 @@ def case_refine_subbox(frames: int = 3) -> None:
     for f in range(frames):
         P.rebuild(v, t, steps, rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=f, accumulate=f > 0)))
     torch.cuda.synchronize()
-    print("refine-subbox ok", rt.counters_dict(P.counters))
+    # one more frame whose refinement counts its work units (the instantiation k_refine<0, 8, 1>)
+    c0 = rt.counters_dict(P.counters)
+    P.rebuild(v, t, steps, rt.make_refine_params(dataclasses.replace(sc.refine, frame_index=frames, accumulate=True),
+                                                 count_work=True))
+    torch.cuda.synchronize()
+    c1 = rt.counters_dict(P.counters)
+    work = {k: c1[k] - c0[k] for k in ("masked_voxels", "node_tests", "reach_tests", "filter_pairs", "exact_tests")}
+    print("refine-subbox ok", work)
 
 
 def case_shadow(coherent: bool = False) -> None:
