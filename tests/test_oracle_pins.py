@@ -434,6 +434,39 @@ def test_resolve_icosphere_close_to_analytic_sphere(orc):
     assert np.all(u_c[m] <= an[m] + math.sqrt(3) + sag)
 
 
+def test_resolve_box_faces_closed_form(orc):
+    """Closed form: a 12-triangle box [8, 16]^3 whose faces lie on voxel planes.  A
+    voxel centre outside the box along exactly one axis is nearest to the face on
+    that side, at distance |p_a - face|; its flooded seed is the seed voxel next to
+    that face, whose representative is a triangle of that face containing the
+    centre's projection, so the coarse distance is exactly that plane distance
+    (every coordinate a multiple of 1/2).  Fails on a wrong closest-point region,
+    a wrong representative choice or a wrong tap in the flooding."""
+    V, T = scenes.box_mesh()
+    V = (V * 4.0 + 12.0).astype(np.float32)
+    g = scenes.Grid(24, 24, 24, (0.0, 0.0, 0.0), 1.0)
+    seed, rep, _ = orc.voxelize(V, T, g)
+    near = orc.jfa(g, seed, scenes.jfa_steps(g))
+    u_c, _ = orc.resolve(g, V, T, near, rep, 3.0)
+    checked = 0
+    for k in range(g.nz):
+        for j in range(g.ny):
+            for i in range(g.nx):
+                p = (i + 0.5, j + 0.5, k + 0.5)
+                out = [c < 8.0 or c > 16.0 for c in p]
+                if sum(out) != 1:
+                    continue
+                a = out.index(True)
+                want = p[a] - 16.0 if p[a] > 16.0 else 8.0 - p[a]
+                s_near = [i, j, k]
+                s_near[a] = 16 if p[a] > 16.0 else 7
+                got_seed = int(near[k, j, i])
+                assert got_seed == (s_near[2] << 20) | (s_near[1] << 10) | s_near[0], (i, j, k)
+                assert u_c[k, j, i] == np.float32(want), (i, j, k, u_c[k, j, i], want)
+                checked += 1
+    assert checked == 6 * 8 * 8 * 8   # six faces, 8 x 8 columns, 8 voxels out to the grid's edge
+
+
 # --------------------------------------------------------------- refinement
 
 def test_refine_plane_hit_distance_distribution(orc):
@@ -720,6 +753,40 @@ def test_shadow_sphere_umbra_and_lit_regions(orc):
     vis = orc.shadow(g, f, pos, nrm, sp)
     assert vis[0] == 0.0 and vis[-1] == 1.0
     assert np.all(np.diff(vis) >= -1e-6)
+
+
+def test_shadow_sphere_umbra_matches_ray_intersection(orc):
+    """Grid SDF of a sphere (radius 8 voxels) and an oblique light: a receiver whose
+    light ray (from its lifted origin, past the start offset) passes through the
+    sphere at least one voxel deep is in the umbra (visibility at most 0.02), and one
+    whose ray keeps k * (distance to the sphere) / t >= 1.5 at every t inside the grid
+    is fully lit (1); both decided in FP64 from the analytic sphere, not the grid."""
+    g = scenes.Grid(64, 64, 64, (0.0, 0.0, 0.0), 1.0)
+    C, R = np.array([32.0, 40.0, 32.0]), 8.0
+    k, j, i = np.meshgrid(*(np.arange(64) + 0.5,) * 3, indexing="ij")
+    f = (np.sqrt((i - C[0]) ** 2 + (j - C[1]) ** 2 + (k - C[2]) ** 2) - R).astype(np.float32)
+    xs = np.arange(4.0, 60.0, 1.0) + 0.25
+    X, Z = np.meshgrid(xs, xs, indexing="ij")
+    pos = np.stack([X.ravel(), np.full(X.size, 2.0), Z.ravel()], 1).astype(np.float32)
+    nrm = np.tile(np.array([[0.0, 1.0, 0.0]], np.float32), (len(pos), 1))
+    sp = scenes.ShadowParams(light_dir=(0.3, 1.0, 0.2), k=8.0, steps=256, max_step_vox=2.0)
+    vis = orc.shadow(g, f, pos, nrm, sp)
+    L = np.array(sp.light_dir) / np.linalg.norm(sp.light_dir)
+    o = pos.astype(np.float64) + sp.normal_offset_vox * nrm
+    t0 = sp.start_offset_vox
+    tc = (C - o) @ L
+    dmin = np.linalg.norm((C - o) - tc[:, None] * L, axis=1)
+    umbra = (tc > t0 + R) & (dmin <= R - 1.0)
+    ts = np.arange(t0, 120.0, 0.05)
+    lit = np.ones(len(pos), bool)
+    for n in range(len(pos)):
+        q = o[n] + ts[:, None] * L
+        inside = np.all((q >= 0.0) & (q <= 64.0), axis=1)
+        d = np.linalg.norm(q[inside] - C, axis=1) - R
+        lit[n] = np.all(sp.k * d / ts[inside] >= 1.5)
+    assert umbra.sum() > 100 and lit.sum() > 100
+    assert np.all(vis[umbra] <= 0.02), vis[umbra].max()
+    assert np.all(vis[lit] == 1.0), vis[lit].min()
 
 
 def _small_sphere_state(orc):
