@@ -2,10 +2,42 @@
 // receiver, sphere tracing toward a directional light with the triangulated
 // penumbra estimate, software trilinear sampling (8 read-only loads + FP32 lerps
 // in x, then y, then z; the hardware filter's fixed-point weights are avoided).
+// The samples and the stop decisions use the same FP32 operations as the adjoint's
+// replay; the penumbra estimate is kept as a fraction (penumbra_step).
 #include "rtsdf_launch.cuh"
 #include "shadow_march.cuh"
 
 namespace rtsdf {
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Running minimum of the triangulated penumbra estimate k e / max(t - y, 1e-6)
+// (Sec. 2.5.2; y = d^2 / (2 d_prev), e = sqrt(max(d^2 - y^2, 0))), held as a fraction
+// rn / rd and compared by cross-multiplication, so a step takes one division (y)
+// instead of two; the single division of the winning fraction comes at the end and
+// reproduces its quotient.  y and the difference d^2 - y^2 (which cancels when d is
+// near 2 d_prev) are the oracle's own FP32 operations; the square root after the
+// cancellation is the approximate one (a few ulp, unamplified), so the visibility
+// stays within a few ulp of the quotient form (it is held to 1e-4 of the oracle).
+// The march's control flow depends on d alone and is unchanged.
+struct Penumbra {
+    float rn, rd;
+};
+
+__device__ __forceinline__ void penumbra_step(Penumbra& p, float k, float d, float d_prev, float t) {
+    const float dd = d * d;
+    const float y = dd / (2.0f * d_prev);
+    const float a = k * sqrt_approx(fmaxf(dd - y * y, 0.0f));
+    const float b = fmaxf(t - y, 1e-6f);
+    if (a * p.rd < p.rn * b) {
+        p.rn = a;
+        p.rd = b;
+    }
+}
 
 __global__ void __launch_bounds__(256) k_shadow(ShadowArgs a, const float* __restrict__ sdf,
                                                 const float* __restrict__ pos, const float* __restrict__ nrm, int P,
@@ -13,22 +45,22 @@ __global__ void __launch_bounds__(256) k_shadow(ShadowArgs a, const float* __res
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const float3 o = march_origin(a, pos, nrm, i);
-    float t = march_start(a, i), res = 1.0f, d_prev = __int_as_float(0x7f800000);
+    float t = march_start(a, i), d_prev = __int_as_float(0x7f800000);
+    Penumbra pen{1.0f, 1.0f};
+    bool hit = false;
     for (int s = 0; s < a.steps; ++s) {
         const float qx = o.x + t * a.L.x, qy = o.y + t * a.L.y, qz = o.z + t * a.L.z;
         if (outside_box(a.g, qx, qy, qz)) break;
         const float d = trilinear(sdf, a.g, qx, qy, qz) - a.bias;
         if (d <= a.hit_eps) {
-            res = 0.0f;
+            hit = true;
             break;
         }
-        const float dd = d * d;
-        const float y = dd / (2.0f * d_prev);
-        const float e = sqrtf(fmaxf(dd - y * y, 0.0f));
-        res = fminf(res, (a.k * e) / fmaxf(t - y, 1e-6f));
+        penumbra_step(pen, a.k, d, d_prev, t);
         d_prev = d;
         t = t + fminf(d, a.max_step);
     }
+    const float res = hit ? 0.0f : pen.rn / pen.rd;
     vis[i] = fminf(fmaxf(res, 0.0f), 1.0f);
 }
 
@@ -84,23 +116,23 @@ __global__ void __launch_bounds__(kCoherentBlock) k_shadow_coherent(ShadowArgs a
     if (t >= n) return;
     const int i = base + perm[t];
     const float3 o = march_origin(a, pos, nrm, i);
-    float tt = march_start(a, i), res = 1.0f, d_prev = __int_as_float(0x7f800000);
+    float tt = march_start(a, i), d_prev = __int_as_float(0x7f800000);
+    Penumbra pen{1.0f, 1.0f};
+    bool hit = false;
     int s = 0;
     for (; s < a.steps; ++s) {
         const float qx = o.x + tt * a.L.x, qy = o.y + tt * a.L.y, qz = o.z + tt * a.L.z;
         if (outside_box(a.g, qx, qy, qz)) break;
         const float d = trilinear(sdf, a.g, qx, qy, qz) - a.bias;
         if (d <= a.hit_eps) {
-            res = 0.0f;
+            hit = true;
             break;
         }
-        const float dd = d * d;
-        const float y = dd / (2.0f * d_prev);
-        const float e = sqrtf(fmaxf(dd - y * y, 0.0f));
-        res = fminf(res, (a.k * e) / fmaxf(tt - y, 1e-6f));
+        penumbra_step(pen, a.k, d, d_prev, tt);
         d_prev = d;
         tt = tt + fminf(d, a.max_step);
     }
+    const float res = hit ? 0.0f : pen.rn / pen.rd;
     vis[i] = fminf(fmaxf(res, 0.0f), 1.0f);
     steps[i] = (uint8_t)min(s, 255);
 }
