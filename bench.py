@@ -935,7 +935,8 @@ def run_sweep(args):
     frames, fresh refine state each frame) over (a) grid size x rays per voxel and (b)
     ray-mask distance x rays per voxel at 256x128x256: the axes of the paper's Table 3
     (size x rays) and Table 4 (mask distance d x rays), on one grid instead of the
-    paper's coarse + fine pair."""
+    paper's coarse + fine pair.  Each point also reports the refinement's counted work per
+    masked voxel (staged triangles reach-tested, pairs within reach) and exact tests per ray."""
     import torch
 
     from paper_2210_06160_gb300 import build
@@ -968,10 +969,20 @@ def run_sweep(args):
                 for j in range(4):
                     acc[j] += ev[j].elapsed_time(ev[j + 1]) / frames
         c = rt.counters_dict(P.counters)
+        # one more refinement that counts its work units (not timed)
+        P.refine(verts, tris, rt.make_refine_params(dataclasses.replace(sc.refine, rays_per_voxel=rays,
+                                                                        mask_vox=mask_vox, accumulate=0),
+                                                    count_work=True))
+        torch.cuda.synchronize()
+        w = rt.counters_dict(P.counters)
+        nm = max(1, w["masked_voxels"] - c["masked_voxels"])
+        work = {"staged_per_voxel": round((w["reach_tests"] - c["reach_tests"]) / nm, 1),
+                "pairs_per_voxel": round((w["filter_pairs"] - c["filter_pairs"]) / nm, 1),
+                "exact_per_ray": round((w["exact_tests"] - c["exact_tests"]) / (nm * rays), 2)}
         del P
         torch.cuda.empty_cache()
         return {"voxelize": round(acc[0], 3), "bvh": round(acc[1], 3), "jfa": round(acc[2], 3),
-                "refine": round(acc[3], 3), "masked_voxels": c["masked_voxels"] // (warmup + frames)}
+                "refine": round(acc[3], 3), "masked_voxels": c["masked_voxels"] // (warmup + frames), **work}
 
     size_rays = []
     for nx in (128, 256, 512):
