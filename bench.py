@@ -804,6 +804,8 @@ def run_ours(args):
     roofline = {"kernel": "k_jfa_pass + k_jfa_pass_grouped (all passes of a frame)", "bound": "hbm", "achieved": round(jfa_gbs, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(jfa_gbs / hbm_peak, 4), "traffic": traffic,
                 "peak_source": peak_src, "algorithmic_bytes_per_frame": jfa_bytes,
+                "per": f"frame: the {len(sc.jfa_steps)} flooding launches together (achieved = their bytes / "
+                       f"their summed time, the launch-weighted mean rate; traffic likewise per frame)",
                 "limit": "instruction issue (27 candidates per voxel, an exact (distance, seed) argmin each), not HBM"}
 
     # the dominant kernel by time, k_refine: the work it counts (rtsdf_counters, one counted frame)
