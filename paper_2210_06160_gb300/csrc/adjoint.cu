@@ -97,9 +97,11 @@ __global__ void __launch_bounds__(256) k_sample_adjoint(GridD g, const float* __
 
 // ------------------------------------------------------------------ shadow
 
-// Adjoint of one receiver's visibility, upstream gradient gv.  Replays the forward
-// march of k_shadow operation for operation (so every decision is the forward's),
-// then walks the steps up to the argmin backwards one checkpoint segment at a time.
+// Adjoint of one receiver's visibility, upstream gradient gv.  Replays the march of
+// k_shadow with its FP32 samples and steps (so every stop and step decision is the
+// forward's) and the penumbra estimate in the quotient form the oracle uses, whose
+// first minimum is the sample the frozen function differentiates; then walks the
+// steps up to that argmin backwards one checkpoint segment at a time.
 // Adds dLoss/d(field) into gsdf and returns dLoss/dL (unit light direction).
 __device__ float3 shadow_pixel_adjoint(const ShadowArgs& a, const float* __restrict__ sdf, float3 o, float t0, float gv,
                                        float* __restrict__ gsdf) {
@@ -121,7 +123,7 @@ __device__ float3 shadow_pixel_adjoint(const ShadowArgs& a, const float* __restr
         const float y = dd / (2.0f * d_prev);
         const float e = sqrtf(fmaxf(dd - y * y, 0.0f));
         const float r = (a.k * e) / fmaxf(t - y, 1e-6f);
-        if (r < res) {  // the forward's running fminf: the first step attaining the minimum
+        if (r < res) {  // the running minimum: the first step attaining it
             res = r;
             argmin = s;
             am_t = t;
