@@ -206,7 +206,7 @@ __global__ void k_bbvh_leaves(const __grid_constant__ BatchTable t, const float*
 struct PassD {
     const uint32_t* in;
     uint32_t* out;
-    int32_t nx, ny, nz, k, nchunk, gbx, gby, block_start;
+    int32_t nx, ny, nz, k, chunk, nchunk, gbx, gby, block_start;
 };
 
 struct PassTable {
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kJX* kJY) k_bjfa_pass(const __grid_constant__ 
     }
     const PassD& e = p.e[lo];
     const int local = b - e.block_start;
-    jfa_column(e.in, e.out, e.nx, e.ny, e.nz, e.k, e.nchunk, kChunk, local % e.gbx, (local / e.gbx) % e.gby,
+    jfa_column(e.in, e.out, e.nx, e.ny, e.nz, e.k, e.nchunk, e.chunk, local % e.gbx, (local / e.gbx) % e.gby,
                local / (e.gbx * e.gby));
 }
 
@@ -461,8 +461,10 @@ rtsdf_status enqueue_jfa(const rtsdf_batch_plan& P, uint32_t* a, uint32_t* b, cu
             e.ny = sc.grid.ny;
             e.nz = sc.grid.nz;
             e.k = sc.steps[idx];
+            // the single-scene rule: 32-plane chunks for grids of 16 M voxels and more, else 16
+            e.chunk = (int64_t)e.nx * e.ny * e.nz >= (int64_t)(16 << 20) ? kChunk : kChunkSmall;
             const int nq = (e.nz + e.k - 1) / e.k;
-            e.nchunk = (nq + kChunk - 1) / kChunk;
+            e.nchunk = (nq + e.chunk - 1) / e.chunk;
             e.gbx = jfa_xblocks(e.nx, e.k);
             e.gby = (e.ny + kJY - 1) / kJY;
             e.block_start = blocks;
