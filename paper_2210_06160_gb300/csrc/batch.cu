@@ -229,8 +229,10 @@ __global__ void __launch_bounds__(kJX* kJY) k_bjfa_pass(const __grid_constant__ 
 
 // ------------------------------------------------------------------ coarse field + refine
 
+// A scene's refinement arguments for bricks of BX x BY x BZ (built on the host into a
+// RefineTable for each launch).
 template <int BX, int BY, int BZ>
-__device__ __forceinline__ RefineArgs scene_args(const SceneD& S, const char* bvh, uint32_t frame, int accumulate) {
+__host__ __device__ inline RefineArgs scene_args(const SceneD& S, const char* bvh, uint32_t frame, int accumulate) {
     RefineArgs a;
     a.g = S.g;
     a.tv = reinterpret_cast<const TriVox*>(bvh + S.bvh_off + bvh_tris_offset(S.T));
@@ -258,6 +260,15 @@ __device__ __forceinline__ RefineArgs scene_args(const SceneD& S, const char* bv
     return a;
 }
 
+// The refinement arguments of every scene for one launch (the brick shape, frame and
+// accumulation mode of that launch), built on the host and passed as a grid-constant
+// kernel parameter: the kernels read a scene's fields from the parameter bank with a
+// warp-uniform index, as the single-scene kernels read their own RefineArgs, instead
+// of assembling them in registers per brick.
+struct RefineTable {
+    RefineArgs a[kMaxBatch];
+};
+
 struct BatchGrids {
     const int32_t* buf_a;
     const int32_t* buf_b;
@@ -271,9 +282,13 @@ struct BatchGrids {
     const char* bvh;
 };
 
+// both tables travel as kernel parameters (at most 32,764 bytes of them per launch)
+static_assert(sizeof(BatchTable) + sizeof(RefineTable) + sizeof(BatchGrids) + 128 <= 32764, "kernel parameters");
+
 template <int BX, int BY, int BZ>
-__global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ BatchTable t, BatchGrids G, uint32_t frame,
-                                                  int accumulate, unsigned long long* __restrict__ bmask,
+__global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ BatchTable t,
+                                                  const __grid_constant__ RefineTable R, BatchGrids G,
+                                                  unsigned long long* __restrict__ bmask,
                                                   int32_t* __restrict__ blist, uint32_t* __restrict__ count) {
     __shared__ unsigned long long smask[kMaxBricksPerTile];
     const int si = RTSDF_FIND_SCENE(t, tile_start, blockIdx.x);
@@ -281,7 +296,7 @@ __global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ Bat
     const int local = blockIdx.x - S.tile_start;
     const int gtx = (S.g.nx + 31) / 32, gty = (S.g.ny + 3) / 4;
     const int3 tb = make_int3(local % gtx, (local / gtx) % gty, local / (gtx * gty));
-    const RefineArgs a = scene_args<BX, BY, BZ>(S, G.bvh, frame, accumulate);
+    const RefineArgs& a = R.a[si];
     const int64_t o = S.vox_off;
     resolve_tile<BX, BY, BZ>(a, tb, (S.flood_b ? G.buf_b : G.buf_a) + o, G.rep_tri + o, G.dist_bits + o, G.front + o,
                              G.back + o, G.sdf + o, bmask + S.brick_off, blist, count, nullptr, nullptr,
@@ -289,8 +304,8 @@ __global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ Bat
 }
 
 template <int BX, int BY, int BZ, int RPL>
-__global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t, BatchGrids G,
-                                                                  uint32_t frame, int accumulate,
+__global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t,
+                                                                  const __grid_constant__ RefineTable R, BatchGrids G,
                                                                   const char* __restrict__ bvh,
                                                                   const unsigned long long* __restrict__ bmask,
                                                                   const int32_t* __restrict__ blist,
@@ -309,7 +324,7 @@ __global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() 
         const uint32_t e = (uint32_t)blist[wk];
         const int si = (int)(e >> kBrickBits), b = (int)(e & ((1u << kBrickBits) - 1u));
         const SceneD& S = t.s[si];
-        const RefineArgs a = scene_args<BX, BY, BZ>(S, G.bvh, frame, accumulate);
+        const RefineArgs& a = R.a[si];
         const BvhHeader* hdr = reinterpret_cast<const BvhHeader*>(bvh + S.bvh_off);
         const BvhNode* nodes = reinterpret_cast<const BvhNode*>(bvh + S.bvh_off + bvh_nodes_offset());
         const BvhLeaf* leaves = reinterpret_cast<const BvhLeaf*>(bvh + S.bvh_off + bvh_leaves_offset(S.T));
@@ -522,6 +537,10 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
                            rtsdf_counters* counters, int warps, cudaStream_t s) {
     const Shape sh{BX, BY, BZ};
     const BatchTable t = make_table(P, sh);
+    RefineTable R;
+    memset(&R, 0, sizeof(R));
+    for (int si = 0; si < t.n; ++si)
+        R.a[si] = scene_args<BX, BY, BZ>(t.s[si], static_cast<const char*>(B.bvh), frame, accumulate);
     char* ws = static_cast<char*>(B.ws);
     auto* count = reinterpret_cast<uint32_t*>(ws + P.off_count);
     auto* bmask = reinterpret_cast<unsigned long long*>(ws + P.off_bmask);
@@ -529,7 +548,7 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     BatchGrids G{B.seed, B.buf_b, B.rep_tri, B.dist_bits, B.front, B.back, B.sdf, B.verts, B.tris,
                  static_cast<const char*>(B.bvh)};
     RTSDF_CUDA(cudaMemsetAsync(count, 0, 16, s));
-    k_bresolve<BX, BY, BZ><<<P.ntiles, 512, 0, s>>>(t, G, frame, accumulate, bmask, blist, count);
+    k_bresolve<BX, BY, BZ><<<P.ntiles, 512, 0, s>>>(t, R, G, bmask, blist, count);
     RTSDF_LAUNCHED();
     const size_t smem = sizeof(WarpSmemT<RPL>) * (size_t)warps;
     static bool attr_set[64] = {false};
@@ -541,7 +560,7 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
         attr_set[dev] = true;
     }
     // the same resident warps per SM for every CTA size (shared memory bound)
-    k_brefine<BX, BY, BZ, RPL><<<num_sms() * (refine_warps_per_sm<RPL>() / warps), 32 * warps, smem, s>>>(t, G, frame, accumulate,
+    k_brefine<BX, BY, BZ, RPL><<<num_sms() * (refine_warps_per_sm<RPL>() / warps), 32 * warps, smem, s>>>(t, R, G,
                                                                             static_cast<const char*>(B.bvh), bmask,
                                                                             blist, count, counters);
     RTSDF_LAUNCHED();
