@@ -310,9 +310,9 @@ __device__ __forceinline__ bool run_item(WarpSmemT<RPL>& w, const BvhLeaf* __res
     const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
     const float3 A = make_float3(v0.x, v0.y, v0.z);
     const float3 e1 = make_float3(e1f.x, e1f.y, e1f.z), e2 = make_float3(e2f.x, e2f.y, e2f.z);
-    float t, margin = 1.0f;
+    float t, margin;
     bool front;
-    const bool hit = kCount ? ray_tri(o, d, A, e1, e2, tmax, t, front, margin) : ray_tri(o, d, A, e1, e2, tmax, t, front);
+    const bool hit = ray_tri_flat(o, d, A, e1, e2, tmax, t, front, margin);
     if (hit) {
         const uint32_t id = (uint32_t)__float_as_int(v0.w);
         const unsigned long long key =

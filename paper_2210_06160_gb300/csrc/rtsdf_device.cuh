@@ -225,6 +225,28 @@ __device__ __forceinline__ bool ray_tri(float3 o, float3 d, float3 A, float3 e1,
     return ray_tri(o, d, A, e1, e2, tmax, t, front, margin);
 }
 
+// The same test without early exits, for lanes of a warp that test different items:
+// every quantity is the FP32 expression above, evaluated unconditionally, and the
+// accept conditions are the negations of the early-exit tests (so a NaN compares
+// exactly as it does there), combined at the end; the result is bit-identical.
+__device__ __forceinline__ bool ray_tri_flat(float3 o, float3 d, float3 A, float3 e1, float3 e2, float tmax,
+                                             float& t, bool& front, float& margin) {
+    const float3 p = cross3(d, e2);
+    const float det = dot3(e1, p);
+    const float inv = 1.0f / det;
+    const float3 tv = sub3(o, A);
+    const float u = dot3(tv, p) * inv;
+    const float3 q = cross3(tv, e1);
+    const float w = dot3(d, q) * inv;
+    const float uw = u + w;
+    const float tt = dot3(e2, q) * inv;
+    const bool hit = det != 0.0f && !(u < 0.0f || u > 1.0f) && !(w < 0.0f || uw > 1.0f) && tt > 0.0f && tt <= tmax;
+    t = tt;
+    front = det > 0.0f;
+    margin = fminf(fminf(u, w), 1.0f - uw);
+    return hit;
+}
+
 // ------------------------------------------------------------------ BVH layout
 
 // Buffer: header, then max(n-1,1) inner nodes, then n leaves (n = triangle count).
