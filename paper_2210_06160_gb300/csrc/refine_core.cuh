@@ -253,7 +253,7 @@ struct WarpSmemT {
     uint32_t queue[RaySlots<RPL>::kQueue];        // (list index << (5 + rbits)) | (slot << rbits) | ray
     int qn;                                      // queued items
     uint32_t okm[32];                            // rays of each slot that drew a direction
-    float4 origin[32];                           // voxel centres of the pass's slots
+    float4 origin[32];                           // voxel centres of the pass's slots (w: linear index)
     float4 dq[3][RaySlots<RPL>::kQuads][32];      // ray directions: [component][ray / 4][slot], rays 4q..4q+3 in x..w
     float4 tsph[32];                             // bounding spheres of the chunk's staged triangles
     float4 tpln[32];                             // their planes
@@ -450,6 +450,52 @@ __device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int b
     __syncwarp();
 }
 
+// Rays of the group whose first draw failed (both candidate pairs of attempt 0
+// rejected, about 4.6% of rays; bit r of `need` in the lane owning the slot) continue
+// from attempt 1, one ray per lane: the warp lists its (slot, ray) items in the item
+// queue, which is unused at this point, so a retry costs one round of draws for up to
+// 32 rays instead of a loop per ray row that nearly every warp would enter.  Each
+// success writes the ray's direction into the slot's row and sets its bit in okm;
+// rays that fail all 32 attempts are counted in n_fail.  Called by the whole warp.
+template <int RPL>
+__device__ __forceinline__ void redraw(WarpSmemT<RPL>& w, uint32_t need, const RefineArgs& a, int r0,
+                                       uint32_t& n_fail) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(need);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - cnt;
+    while (need) {
+        const int r = __ffs(need) - 1;
+        need &= need - 1u;
+        w.queue[pos++] = ((uint32_t)lane << 5) | (uint32_t)r;
+    }
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+        if (b + lane < total) {
+            const uint32_t it = w.queue[b + lane];
+            const int slot = (int)(it >> 5), r = (int)(it & 31u);
+            const uint32_t vox = (uint32_t)__float_as_int(w.origin[slot].w);
+            float3 d;
+            if (sphere_dir(vox, a.frame * (uint32_t)a.R + (uint32_t)(r0 + r), a.scene, a.k0, a.k1, d, 1u)) {
+                float* row = reinterpret_cast<float*>(&w.dq[0][r >> 2][slot]);
+                row[r & 3] = d.x;
+                reinterpret_cast<float*>(&w.dq[1][r >> 2][slot])[r & 3] = d.y;
+                reinterpret_cast<float*>(&w.dq[2][r >> 2][slot])[r & 3] = d.z;
+                atomicOr(&w.okm[slot], 1u << r);
+            } else {
+                ++n_fail;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // One warp refines one brick (bx, by, bz) whose masked voxels are the set bits of
 // m; lane l owns voxel slot (pass*32 + l) and draws up to 8 rays of it per group.
 // The brick's staged triangles are taken 32 at a time (one per lane): every
@@ -522,7 +568,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             clin = coarse_index(a, i, j, k, ic, jc, kc);
             o = make_float3((float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f);
         }
-        w.origin[lane] = make_float4(o.x, o.y, o.z, 0.f);
+        w.origin[lane] = make_float4(o.x, o.y, o.z, __int_as_float(lin));  // w: the voxel's linear index
         const int nv = min(32, nm - pass * 32);
         uint32_t vbest = 0xffffffffu, vfront = 0, vback = 0;
         // tracked: this call's winning ray, ordered by (t, triangle id), first ray on ties
@@ -530,17 +576,17 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
         uint32_t wray = 0xFFFFFFFFu;
         for (int r0 = 0; r0 < a.R; r0 += RPL) {
             float3 dir[RPL];
-            uint32_t okm = 0;
+            uint32_t okm = 0, need = 0;
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
                 const int ray = r0 + r;
                 dir[r] = make_float3(0.f, 0.f, 1.f);
                 if (mine && ray < a.R) {
-                    if (sphere_dir((uint32_t)lin, a.frame * (uint32_t)a.R + (uint32_t)ray, a.scene, a.k0, a.k1,
-                                   dir[r]))
+                    if (sphere_dir_first((uint32_t)lin, a.frame * (uint32_t)a.R + (uint32_t)ray, a.scene, a.k0,
+                                         a.k1, dir[r]))
                         okm |= 1u << r;
                     else
-                        ++n_fail;
+                        need |= 1u << r;
                 }
                 w.key[r][lane] = ~0ull;
             }
@@ -558,6 +604,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                 for (int k = 0; k < 3; ++k) w.dq[k][q][lane] = make_float4(c[k][0], c[k][1], c[k][2], c[k][3]);
             }
             w.okm[lane] = okm;
+            if (__any_sync(0xffffffffu, need != 0u)) redraw<RPL>(w, need, a, r0, n_fail);
             int sp = 0;
             if (!complete && n_leaves > 0) {
                 if (lane == 0) w.stack[0] = 0;
