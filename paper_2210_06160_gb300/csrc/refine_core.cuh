@@ -255,8 +255,9 @@ struct WarpSmemT {
     uint32_t okm[32];                            // rays of each slot that drew a direction
     float4 origin[32];                           // voxel centres of the pass's slots (w: linear index)
     float4 dq[3][RaySlots<RPL>::kQuads][32];      // ray directions: [component][ray / 4][slot], rays 4q..4q+3 in x..w
-    float4 tsph[32];                             // bounding spheres of the chunk's staged triangles
+    float4 tsph[32];                             // bounding spheres of the chunk's staged triangles (w: radius^2)
     float4 tpln[32];                             // their planes
+    float2 tcon[32];                             // their filter constants (near cone threshold, plane margin)
     uint16_t pairs[160];                         // (slot << 5) | chunk lane: (voxel, triangle) pairs to filter
     unsigned long long key[RaySlots<RPL>::kRays][32];  // closest hit: (t bits << 32) | (id << 1) | front
     unsigned long long work[4];                  // node, reach, filter-pair and exact-test counts (lane 0 writes)
@@ -373,19 +374,17 @@ template <int RPL>
 __device__ __forceinline__ uint32_t filter_pair(const WarpSmemT<RPL>& w, int v, int j, float tmax, float inv_tmax) {
     constexpr int kQ = (RPL + 3) / 4;
     const float4 o = w.origin[v];
-    const float4 sph = w.tsph[j], pl = w.tpln[j];
+    const float4 sph = w.tsph[j], pl = w.tpln[j];  // sph.w: rho^2
+    const float2 tk = w.tcon[j];
     const float dcx = sph.x - o.x, dcy = sph.y - o.y, dcz = sph.z - o.z;
     const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
-    const float rho = sph.w;
-    const float rho2 = rho * rho;
     // v * rsqrt(v) is within a few ulp of sqrt(v) (a few 1e-7 relative), well inside the
-    // 1e-6 relative and 1e-4 absolute margins, so the threshold stays below the exact one
-    const float v2 = dd - rho2;
-    const float thr = dd > 2.0f * rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho * 1.000001f - 1e-4f;
+    // 1e-6 relative and 1e-4 absolute margins, so the threshold stays below the exact one;
+    // v2 > rho^2 (the origin farther than about rho sqrt(2)) keeps v2 well above 0
+    const float v2 = dd - sph.w;
+    const float thr = v2 > sph.w ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : tk.x;
     const float sd = pl.w - __fmaf_rn(pl.x, o.x, __fmaf_rn(pl.y, o.y, pl.z * o.z));
-    const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
-    const float marg = __fmaf_rn(eps * eps, inv_tmax, 1.5f * eps);
-    const float bq = __fmaf_rn(sd * inv_tmax, sd, -marg);
+    const float bq = __fmaf_rn(sd * inv_tmax, sd, -tk.y);
     const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
     const float2 mx2 = make_float2(sd * pl.x, sd * pl.x), my2 = make_float2(sd * pl.y, sd * pl.y),
                  mz2 = make_float2(sd * pl.z, sd * pl.z);
@@ -448,6 +447,29 @@ __device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int b
         }
     }
     __syncwarp();
+}
+
+// Position of the n-th set bit (from 0) of m, n < popc(m): a binary search on
+// population counts, the same few steps in every lane.
+__device__ __forceinline__ int nth_set_bit(unsigned long long m, int n) {
+    int pos = 0;
+    uint32_t x = (uint32_t)m;
+    const int lo = __popc(x);
+    if (n >= lo) {
+        n -= lo;
+        x = (uint32_t)(m >> 32);
+        pos = 32;
+    }
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc(x & ((1u << w) - 1u));
+        if (n >= c) {
+            n -= c;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
 }
 
 // Rays of the group whose first draw failed (both candidate pairs of attempt 0
@@ -552,16 +574,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
         int64_t clin = 0;  // coarse voxel of the slot (its flooded seed)
         float3 o = make_float3(0.f, 0.f, 0.f);
         if (mine) {
-            // position of the slot-th set bit of the brick mask
-            unsigned long long mm = m;
-            int skip = slot;
-            const int lo_cnt = __popc((uint32_t)mm);
-            if (skip >= lo_cnt) {
-                skip -= lo_cnt;
-                mm &= 0xffffffff00000000ull;
-            }
-            for (int c = 0; c < skip; ++c) mm &= mm - 1ull;
-            const int bit = __ffsll((long long)mm) - 1;
+            const int bit = nth_set_bit(m, slot);
             const int i = bx * BX + bit % BX, j = by * BY + (bit / BX) % BY, k = bz * BZ + bit / (BX * BY);
             lin = (int)(((int64_t)k * a.g.ny + j) * a.g.nx + i);
             int ic, jc, kc;
@@ -634,8 +647,14 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                     if (c < nc) {
                         const BvhLeaf* L = leaves + w.list[c];
                         sph = __ldg(&L->sph);
-                        w.tsph[lane] = sph;
-                        w.tpln[lane] = __ldg(&L->pln);
+                        const float4 pl = __ldg(&L->pln);
+                        w.tsph[lane] = make_float4(sph.x, sph.y, sph.z, sph.w * sph.w);
+                        w.tpln[lane] = pl;
+                        // the filter's per-triangle constants: the near cone threshold
+                        // -rho (widened) and the plane margin 1.5 eps + eps^2 / tmax
+                        const float eps = 2e-3f + 2e-6f * fabsf(pl.w);
+                        w.tcon[lane] = make_float2(-sph.w * 1.000001f - 1e-4f,
+                                                   __fmaf_rn(eps * eps, inv_tmax, 1.5f * eps));
                         const float reach = sph.w + a.tmax;
                         reach2 = reach * reach;
                     }
