@@ -14,7 +14,7 @@
 
 namespace rtsdf {
 
-constexpr int kChunk = 16;  // items per warp chunk
+constexpr int kChunk = 32;  // items per warp chunk (one per lane)
 
 // Per triangle: number of bricks its voxel range touches (0 if invalid or outside).
 __global__ void k_vox_count(const float* __restrict__ verts, int V, const int32_t* __restrict__ tris, int T,
@@ -48,19 +48,7 @@ __global__ void __launch_bounds__(256) k_vox_test(const float* __restrict__ vert
             const int mid = (lo + hi + 1) >> 1;
             if (offsets[mid] <= i0) lo = mid; else hi = mid - 1;
         }
-        int t = lo;
-        float3 a, b, c;
-        TriRange r;
-        bool have = false;
-        for (uint64_t item = i0; item < i1; ++item) {
-            while (offsets[t + 1] <= item) { ++t; have = false; }
-            if (!have) {
-                load_tri(verts, V, tris, t, g, a, b, c);  // count > 0 implies valid
-                tri_range(a, b, c, g, r);
-                have = true;
-            }
-            vox_item(a, b, c, r, (int)(item - offsets[t]), t, g, keys);
-        }
+        vox_chunk(verts, V, tris, T, g, offsets, i0, (int)(i1 - i0), lo, keys);
     }
 }
 

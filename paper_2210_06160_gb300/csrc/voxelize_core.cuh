@@ -142,4 +142,122 @@ __device__ __forceinline__ void vox_item(float3 a, float3 b, float3 c, const Tri
     }
 }
 
+// The items [i0, i0 + n) (n <= 32) of one warp chunk, item i0 in triangle t0, one
+// item per lane.  Each lane finds its item's triangle (a search over the chunk's
+// triangle offsets), loads it and culls its brick; the surviving small items (and
+// slivers) are then packed, their (triangle, voxel) tests spread over the lanes 32
+// at a time, so no lane idles on a brick with few voxels in range, and the brick
+// culls run side by side instead of one per warp step.  Items with many voxels and
+// a well-shaped triangle take vox_item's warp-wide plane filter, one at a time.
+// Every (triangle, voxel) pair vox_item would test is tested once, with the same
+// separating-axis test and key, so the keys are the same.
+__device__ __forceinline__ void vox_chunk(const float* __restrict__ verts, int V, const int32_t* __restrict__ tris,
+                                          int T, const GridD& g, const uint64_t* __restrict__ offsets, uint64_t i0,
+                                          int n, int t0, unsigned long long* __restrict__ keys) {
+    const int lane = (int)lane_id();
+    const uint64_t item = i0 + (uint64_t)lane;
+    const bool has = lane < n;
+    // triangle of the lane's item: t0 + #{j < 32 : offsets[t0 + j + 1] <= item}, the
+    // chunk's triangle end offsets held one per lane
+    const uint64_t endl = t0 + lane < T ? offsets[t0 + lane + 1] : ~0ull;
+    const uint64_t e31 = __shfl_sync(0xffffffffu, endl, 31);
+    int cnt = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint64_t e = __shfl_sync(0xffffffffu, endl, cnt + step - 1);
+        if (e <= item) cnt += step;
+    }
+    if (e31 <= item) cnt = 32;
+    int t = t0 + cnt;
+    if (has && cnt == 32)
+        while (offsets[t + 1] <= item) ++t;  // a chunk spanning more than 32 triangles (empty ones between)
+    float3 a = make_float3(0.f, 0.f, 0.f), b = a, c = a;
+    TriRange r{};
+    int local = 0;
+    bool keep = false, big = false;
+    int x0 = 0, y0 = 0, z0 = 0, sx = 1, sy = 1, nsub = 0;
+    if (has) {
+        load_tri(verts, V, tris, t, g, a, b, c);  // count > 0 implies valid
+        tri_range(a, b, c, g, r);
+        local = (int)(item - offsets[t]);
+        const int nbx = r.hi[0] / kBrick - r.lo[0] / kBrick + 1;
+        const int nby = r.hi[1] / kBrick - r.lo[1] / kBrick + 1;
+        const int bx = r.lo[0] / kBrick + local % nbx;
+        const int by = r.lo[1] / kBrick + (local / nbx) % nby;
+        const int bz = r.lo[2] / kBrick + local / (nbx * nby);
+        const float3 bc = make_float3((float)(bx * kBrick) + 0.5f * kBrick, (float)(by * kBrick) + 0.5f * kBrick,
+                                      (float)(bz * kBrick) + 0.5f * kBrick);
+        keep = tri_box_overlap(a, b, c, bc, 0.5f * kBrick + 0.0625f);
+        x0 = max(r.lo[0], bx * kBrick);
+        y0 = max(r.lo[1], by * kBrick);
+        z0 = max(r.lo[2], bz * kBrick);
+        sx = min(r.hi[0], bx * kBrick + kBrick - 1) - x0 + 1;
+        sy = min(r.hi[1], by * kBrick + kBrick - 1) - y0 + 1;
+        nsub = sx * sy * (min(r.hi[2], bz * kBrick + kBrick - 1) - z0 + 1);
+        if (keep && nsub > 2 * kWarp) {
+            const float3 e1 = sub3(b, a), e2 = sub3(c, a);
+            const float3 nn = cross3(e1, e2);
+            const float len2 = dot3(nn, nn);
+            const float sin2 = len2 / (dot3(e1, e1) * dot3(e2, e2));
+            big = sin2 > 1e-8f && isfinite(len2);  // the plane-filtered path of vox_item
+        }
+    }
+    // big items: vox_item, the whole warp on one item
+    uint32_t bm = __ballot_sync(0xffffffffu, big);
+    while (bm) {
+        const int src = __ffs(bm) - 1;
+        bm &= bm - 1u;
+        const float3 ba = make_float3(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src),
+                                      __shfl_sync(0xffffffffu, a.z, src));
+        const float3 bb = make_float3(__shfl_sync(0xffffffffu, b.x, src), __shfl_sync(0xffffffffu, b.y, src),
+                                      __shfl_sync(0xffffffffu, b.z, src));
+        const float3 bcv = make_float3(__shfl_sync(0xffffffffu, c.x, src), __shfl_sync(0xffffffffu, c.y, src),
+                                       __shfl_sync(0xffffffffu, c.z, src));
+        TriRange br;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            br.lo[d] = __shfl_sync(0xffffffffu, r.lo[d], src);
+            br.hi[d] = __shfl_sync(0xffffffffu, r.hi[d], src);
+        }
+        vox_item(ba, bb, bcv, br, __shfl_sync(0xffffffffu, local, src), __shfl_sync(0xffffffffu, t, src), g, keys);
+    }
+    // small items and slivers: their voxel tests packed over the lanes
+    const int nl = keep && !big ? nsub : 0;
+    int incl = nl;
+#pragma unroll
+    for (int off = 1; off < kWarp; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+    const int excl = incl - nl;
+    // v / sx and v / sy as (v * ceil(2^16 / s)) >> 16: exact for v < 4096 and s <= 8
+    const int rx = (65536 + sx - 1) / sx, ry = (65536 + sy - 1) / sy;
+    for (int base = 0; base < total; base += kWarp) {
+        const int q = base + lane;
+        int owner = 0;  // last lane whose exclusive count is <= q
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, owner + step);
+            if (e <= q) owner += step;
+        }
+        const float3 oa = make_float3(__shfl_sync(0xffffffffu, a.x, owner), __shfl_sync(0xffffffffu, a.y, owner),
+                                      __shfl_sync(0xffffffffu, a.z, owner));
+        const float3 ob = make_float3(__shfl_sync(0xffffffffu, b.x, owner), __shfl_sync(0xffffffffu, b.y, owner),
+                                      __shfl_sync(0xffffffffu, b.z, owner));
+        const float3 oc = make_float3(__shfl_sync(0xffffffffu, c.x, owner), __shfl_sync(0xffffffffu, c.y, owner),
+                                      __shfl_sync(0xffffffffu, c.z, owner));
+        const int ox = __shfl_sync(0xffffffffu, x0, owner), oy = __shfl_sync(0xffffffffu, y0, owner),
+                  oz = __shfl_sync(0xffffffffu, z0, owner);
+        const int osx = __shfl_sync(0xffffffffu, sx, owner), osy = __shfl_sync(0xffffffffu, sy, owner);
+        const int orx = __shfl_sync(0xffffffffu, rx, owner), ory = __shfl_sync(0xffffffffu, ry, owner);
+        const int ot = __shfl_sync(0xffffffffu, t, owner), oe = __shfl_sync(0xffffffffu, excl, owner);
+        if (q < total) {
+            const int v = q - oe;
+            const int q1 = (v * orx) >> 16, q2 = (q1 * ory) >> 16;
+            vox_voxel(oa, ob, oc, ox + v - q1 * osx, oy + q1 - q2 * osy, oz + q2, ot, g, keys);
+        }
+    }
+}
+
 }  // namespace rtsdf
