@@ -31,7 +31,7 @@ namespace rtsdf {
 
 constexpr int kMaxBatch = RTSDF_BATCH_MAX_SCENES;
 constexpr int kBrickBits = 25;  // brick index bits of a work-list entry
-constexpr int kVoxChunk = 16;   // (triangle, brick) items per warp chunk
+constexpr int kVoxChunk = 32;   // (triangle, brick) items per warp chunk (one per lane)
 
 struct SceneD {
     GridD g;
@@ -84,7 +84,7 @@ __global__ void k_bvox_count(const __grid_constant__ BatchTable t, const float* 
     counts[gt] = n;
 }
 
-__global__ void __launch_bounds__(256) k_bvox_test(const __grid_constant__ BatchTable t,
+__global__ void __launch_bounds__(256, 3) k_bvox_test(const __grid_constant__ BatchTable t,
                                                    const float* __restrict__ verts, const int32_t* __restrict__ tris,
                                                    int Ttot, const uint64_t* __restrict__ offsets,
                                                    unsigned long long* __restrict__ keys) {
@@ -99,22 +99,18 @@ __global__ void __launch_bounds__(256) k_bvox_test(const __grid_constant__ Batch
             const int mid = (lo + hi + 1) >> 1;
             if (offsets[mid] <= i0) lo = mid; else hi = mid - 1;
         }
-        int gt = lo;
-        float3 a, b, c;
-        TriRange r;
-        const SceneD* S = nullptr;
-        bool have = false;
-        for (uint64_t item = i0; item < i1; ++item) {
-            while (offsets[gt + 1] <= item) { ++gt; have = false; }
-            if (!have) {
-                S = &t.s[RTSDF_FIND_SCENE(t, tri_off, gt)];
-                load_tri(verts + 3 * (int64_t)S->vert_off, S->V, tris + 3 * (int64_t)S->tri_off, gt - S->tri_off,
-                         S->g, a, b, c);  // count > 0 implies valid
-                tri_range(a, b, c, S->g, r);
-                have = true;
-            }
-            vox_item(a, b, c, r, (int)(item - offsets[gt]), gt - S->tri_off, S->g, keys + S->vox_off);
-        }
+        vox_chunk<false>(Ttot, offsets, i0, (int)(i1 - i0), lo,
+                  [&](int gt, float3& a, float3& b, float3& c, TriRange& r, int& tnx, int& tny,
+                      unsigned long long*& tk, int& id) {
+                      const SceneD& S = t.s[RTSDF_FIND_SCENE(t, tri_off, gt)];
+                      load_tri(verts + 3 * (int64_t)S.vert_off, S.V, tris + 3 * (int64_t)S.tri_off, gt - S.tri_off,
+                               S.g, a, b, c);  // count > 0 implies valid
+                      tri_range(a, b, c, S.g, r);
+                      tnx = S.g.nx;
+                      tny = S.g.ny;
+                      tk = keys + S.vox_off;
+                      id = gt - S.tri_off;
+                  });
     }
 }
 

@@ -185,18 +185,23 @@ __device__ __forceinline__ void jfa_load(const uint32_t* __restrict__ row, int64
 }
 
 // One plane of the stream: its taps s give three groups: lo and mid merge into the
-// accumulators of outputs p - 1 and p, hi becomes that of output p + 1.
+// accumulators of outputs p - 1 and p, hi becomes that of output p + 1.  A group
+// whose output the thread does not store is skipped (nlo, nmid, nhi false;
+// warp-uniform): the grouped passes of the largest offsets use this at the ends of
+// their short residue classes; the streaming passes compute every group, as the
+// branches cost more there than the halo groups they would skip.
 template <int K, int NR>
 __device__ __forceinline__ void jfa_plane(const uint32_t (&s)[3 * NR], float cxy, float cy, float cz,
-                                          unsigned long long& lo, unsigned long long& mid, unsigned long long& hi) {
+                                          unsigned long long& lo, unsigned long long& mid, unsigned long long& hi,
+                                          bool nlo, bool nmid, bool nhi) {
     constexpr int N = 3 * NR, NP = (N + 1) / 2;
     float2 P[NP], dlo[NP], dhi[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i)
         tap_dist2<K>(s[2 * i], s[2 * i + 1 < N ? 2 * i + 1 : 2 * i], cxy, cy, cz, P[i], dlo[i], dhi[i]);
-    merge_min(lo, group_min<N>(dlo, s));
-    merge_min(mid, group_min<N>(P, s));
-    hi = group_min<N>(dhi, s);
+    if (nlo) merge_min(lo, group_min<N>(dlo, s));
+    if (nmid) merge_min(mid, group_min<N>(P, s));
+    hi = nhi ? group_min<N>(dhi, s) : ~0ull;
 }
 
 // One thread: the outputs (x, y, rz + p K), p in [q0, q1), of one residue class mod
@@ -233,7 +238,9 @@ __device__ __forceinline__ void jfa_col(const uint32_t* __restrict__ in, uint32_
         } else if (p <= pb) {
             jfa_load<K, NR, INTERIOR>(row, rstep, co, cur);
         }
-        if (p <= pb) jfa_plane<K, NR>(cur, cxy, cy, cz, lo, mid, hi);
+        if (p <= pb)
+            jfa_plane<K, NR>(cur, cxy, cy, cz, lo, mid, hi, PREFETCH || (p > q0 && p <= q1),
+                             PREFETCH || (p >= q0 && p < q1), PREFETCH || (p + 1 >= q0 && p + 1 < q1));
         if (p - 1 >= q0 && p - 1 < q1) *o = (uint32_t)lo;
         row += zstep;
         o += zstep;

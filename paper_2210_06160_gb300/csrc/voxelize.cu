@@ -32,7 +32,7 @@ __global__ void k_vox_count(const float* __restrict__ verts, int V, const int32_
     counts[t] = n;
 }
 
-__global__ void __launch_bounds__(256) k_vox_test(const float* __restrict__ verts, int V,
+__global__ void __launch_bounds__(256, 3) k_vox_test(const float* __restrict__ verts, int V,
                                                   const int32_t* __restrict__ tris, int T, GridD g,
                                                   const uint64_t* __restrict__ offsets,  // T+1 exclusive scan
                                                   unsigned long long* __restrict__ keys) {
@@ -48,7 +48,17 @@ __global__ void __launch_bounds__(256) k_vox_test(const float* __restrict__ vert
             const int mid = (lo + hi + 1) >> 1;
             if (offsets[mid] <= i0) lo = mid; else hi = mid - 1;
         }
-        vox_chunk(verts, V, tris, T, g, offsets, i0, (int)(i1 - i0), lo, keys);
+        vox_chunk<true>(T, offsets, i0, (int)(i1 - i0), lo,
+                  [&](int t, float3& a, float3& b, float3& c, TriRange& r, int& tnx, int& tny,
+                      unsigned long long*& tk, int& id) {
+                      load_tri(verts, V, tris, t, g, a, b, c);  // count > 0 implies valid
+                      tri_range(a, b, c, g, r);
+                      tnx = g.nx;
+                      tny = g.ny;
+                      tk = keys;
+                      id = t;
+                  },
+                  g.nx, g.ny, keys);
     }
 }
 

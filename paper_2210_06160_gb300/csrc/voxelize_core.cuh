@@ -150,10 +150,17 @@ __device__ __forceinline__ void vox_item(float3 a, float3 b, float3 c, const Tri
 // culls run side by side instead of one per warp step.  Items with many voxels and
 // a well-shaped triangle take vox_item's warp-wide plane filter, one at a time.
 // Every (triangle, voxel) pair vox_item would test is tested once, with the same
-// separating-axis test and key, so the keys are the same.
-__device__ __forceinline__ void vox_chunk(const float* __restrict__ verts, int V, const int32_t* __restrict__ tris,
-                                          int T, const GridD& g, const uint64_t* __restrict__ offsets, uint64_t i0,
-                                          int n, int t0, unsigned long long* __restrict__ keys) {
+// separating-axis test and key, so the keys are the same.  fetch(t, a, b, c, r, nx, ny,
+// keys, id) loads item triangle t (a valid triangle: it has items) with its voxel
+// range, and names the grid, key array and triangle id its keys take (one scene, or
+// the triangle's scene in a batch).  vox_item and vox_voxel use only the grid's nx
+// and ny (the key index), so those are what the lanes exchange.
+// With kOneGrid every triangle takes the grid (nx1, ny1) and the keys keys1, so the
+// lanes exchange nothing of them.
+template <bool kOneGrid, class Fetch>
+__device__ __forceinline__ void vox_chunk(int T, const uint64_t* __restrict__ offsets, uint64_t i0, int n, int t0,
+                                          Fetch&& fetch, int nx1 = 0, int ny1 = 0,
+                                          unsigned long long* keys1 = nullptr) {
     const int lane = (int)lane_id();
     const uint64_t item = i0 + (uint64_t)lane;
     const bool has = lane < n;
@@ -173,12 +180,14 @@ __device__ __forceinline__ void vox_chunk(const float* __restrict__ verts, int V
         while (offsets[t + 1] <= item) ++t;  // a chunk spanning more than 32 triangles (empty ones between)
     float3 a = make_float3(0.f, 0.f, 0.f), b = a, c = a;
     TriRange r{};
+    int gnx = 1, gny = 1;  // the grid's row and plane sizes (all vox_voxel needs of it)
+    unsigned long long* keys = nullptr;
+    int id = 0;
     int local = 0;
     bool keep = false, big = false;
     int x0 = 0, y0 = 0, z0 = 0, sx = 1, sy = 1, nsub = 0;
     if (has) {
-        load_tri(verts, V, tris, t, g, a, b, c);  // count > 0 implies valid
-        tri_range(a, b, c, g, r);
+        fetch(t, a, b, c, r, gnx, gny, keys, id);
         local = (int)(item - offsets[t]);
         const int nbx = r.hi[0] / kBrick - r.lo[0] / kBrick + 1;
         const int nby = r.hi[1] / kBrick - r.lo[1] / kBrick + 1;
@@ -219,7 +228,12 @@ __device__ __forceinline__ void vox_chunk(const float* __restrict__ verts, int V
             br.lo[d] = __shfl_sync(0xffffffffu, r.lo[d], src);
             br.hi[d] = __shfl_sync(0xffffffffu, r.hi[d], src);
         }
-        vox_item(ba, bb, bcv, br, __shfl_sync(0xffffffffu, local, src), __shfl_sync(0xffffffffu, t, src), g, keys);
+        const GridD bg{kOneGrid ? nx1 : __shfl_sync(0xffffffffu, gnx, src),
+                       kOneGrid ? ny1 : __shfl_sync(0xffffffffu, gny, src), 1, 0.f, 0.f, 0.f, 1.f};
+        unsigned long long* bk = kOneGrid ? keys1
+                                          : reinterpret_cast<unsigned long long*>(__shfl_sync(
+                                                0xffffffffu, reinterpret_cast<uintptr_t>(keys), src));
+        vox_item(ba, bb, bcv, br, __shfl_sync(0xffffffffu, local, src), __shfl_sync(0xffffffffu, id, src), bg, bk);
     }
     // small items and slivers: their voxel tests packed over the lanes
     const int nl = keep && !big ? nsub : 0;
@@ -251,11 +265,16 @@ __device__ __forceinline__ void vox_chunk(const float* __restrict__ verts, int V
                   oz = __shfl_sync(0xffffffffu, z0, owner);
         const int osx = __shfl_sync(0xffffffffu, sx, owner), osy = __shfl_sync(0xffffffffu, sy, owner);
         const int orx = __shfl_sync(0xffffffffu, rx, owner), ory = __shfl_sync(0xffffffffu, ry, owner);
-        const int ot = __shfl_sync(0xffffffffu, t, owner), oe = __shfl_sync(0xffffffffu, excl, owner);
+        const int oid = __shfl_sync(0xffffffffu, id, owner), oe = __shfl_sync(0xffffffffu, excl, owner);
+        const GridD og{kOneGrid ? nx1 : __shfl_sync(0xffffffffu, gnx, owner),
+                       kOneGrid ? ny1 : __shfl_sync(0xffffffffu, gny, owner), 1, 0.f, 0.f, 0.f, 1.f};
+        unsigned long long* ok = kOneGrid ? keys1
+                                          : reinterpret_cast<unsigned long long*>(__shfl_sync(
+                                                0xffffffffu, reinterpret_cast<uintptr_t>(keys), owner));
         if (q < total) {
             const int v = q - oe;
             const int q1 = (v * orx) >> 16, q2 = (q1 * ory) >> 16;
-            vox_voxel(oa, ob, oc, ox + v - q1 * osx, oy + q1 - q2 * osy, oz + q2, ot, g, keys);
+            vox_voxel(oa, ob, oc, ox + v - q1 * osx, oy + q1 - q2 * osy, oz + q2, oid, og, ok);
         }
     }
 }
