@@ -601,7 +601,9 @@ def bench_backward(dev, steps: int = 10, warmup: int = 3) -> dict:
     tracked = rt.Pipeline(g, len(sc.verts), len(sc.tris), device=dev, track=True)
     s_tgt = torch.zeros(len(ds.pts), dtype=torch.float32, device=dev)
     v_tgt = torch.full((len(sc.recv_pos),), 0.5, dtype=torch.float32, device=dev)
-    light = torch.tensor(sc.shadow.light_dir, dtype=torch.float32, requires_grad=True)
+    # the light lives on the GPU, as a trained parameter would: the kernels read it there, so
+    # the forward and backward enqueue without a host round trip
+    light = torch.tensor(sc.shadow.light_dir, dtype=torch.float32, device=dev, requires_grad=True)
     stream = torch.cuda.current_stream()
 
     def plain_fwd():

@@ -92,6 +92,11 @@ typedef struct {
     float jitter_vox;        /* Sec. 2.5.2 jitter: receiver i starts at start_offset + jitter * u_i */
     uint32_t frame_index;    /* u_i in [0, 1) from Philox4x32-10 on counter (i, frame_index, 0x4A177E2, 0),
                                 key (0x51AD0, 0x7E2): the top 24 bits of the first word times 2^-24 */
+    const float* light_dir_device; /* NULL, or a DEVICE pointer (4-byte aligned) to 3 floats used instead
+                                      of light_dir: read by the kernels when they run (stream order), so
+                                      a light that lives on the GPU (a trained parameter) needs no copy to
+                                      the host; normalised on the device with the same FP32 operations.
+                                      Not validated: a zero or non-finite vector gives NaN visibilities. */
 } rtsdf_shadow_params;
 
 /* Device-side counters; each call adds to the fields it owns.  The caller zeroes

@@ -206,10 +206,11 @@ __device__ float3 shadow_pixel_adjoint(const ShadowArgs& a, const float* __restr
     return gL;
 }
 
-__global__ void __launch_bounds__(128) k_shadow_adjoint(ShadowArgs a, const float* __restrict__ sdf,
+__global__ void __launch_bounds__(128) k_shadow_adjoint(ShadowArgs a_in, const float* __restrict__ sdf,
                                                         const float* __restrict__ pos, const float* __restrict__ nrm,
                                                         int P, const float* __restrict__ d_vis,
                                                         float* __restrict__ gsdf, double* __restrict__ gl) {
+    const ShadowArgs a = with_light(a_in);
     __shared__ float red[3][4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float3 g = make_float3(0.0f, 0.0f, 0.0f);
@@ -238,8 +239,10 @@ __global__ void __launch_bounds__(128) k_shadow_adjoint(ShadowArgs a, const floa
 
 // dLoss/dl for the unnormalised light direction l = |l| L:
 // (gL - L (L . gL)) / |l|.
-__global__ void k_light_finalize(const double* __restrict__ gl, float3 L, float len, float* __restrict__ d_light) {
+__global__ void k_light_finalize(const double* __restrict__ gl, float3 L, float len, const float* __restrict__ Ldev,
+                                 float* __restrict__ d_light) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (Ldev) L = unit_light(Ldev, len);  // the caller's device light vector
     const double lx = L.x, ly = L.y, lz = L.z;
     const double LgL = lx * gl[0] + ly * gl[1] + lz * gl[2];
     d_light[0] = (float)((gl[0] - lx * LgL) / (double)len);
@@ -483,8 +486,8 @@ rtsdf_status backward(const rtsdf_grid& gh, const float* verts, int32_t V, const
                                                      d_verts);
     RTSDF_LAUNCHED();
     const float* l = sp.light_dir;
-    const float len = sqrtf(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
-    k_light_finalize<<<1, 32, 0, s>>>(w.gl, sa.L, len, d_light);
+    const float len = sp.light_dir_device ? 0.0f : sqrtf(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    k_light_finalize<<<1, 32, 0, s>>>(w.gl, sa.L, len, sp.light_dir_device, d_light);
     RTSDF_LAUNCHED();
     return RTSDF_OK;
 }

@@ -144,10 +144,16 @@ bool refine_params_ok(const rtsdf_refine_params* p) {
 
 bool shadow_params_ok(const rtsdf_shadow_params* p) {
     if (!p) return false;
-    const float* l = p->light_dir;
-    const float len2 = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
-    return len2 > 0.0f && isfinite(len2) && p->steps >= 0 && p->max_step_vox > 0.0f && isfinite(p->k) &&
-           p->jitter_vox >= 0.0f && isfinite(p->jitter_vox);
+    bool light_ok;
+    if (p->light_dir_device) {
+        light_ok = reinterpret_cast<uintptr_t>(p->light_dir_device) % 4 == 0;  // read on the device
+    } else {
+        const float* l = p->light_dir;
+        const float len2 = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
+        light_ok = len2 > 0.0f && isfinite(len2);
+    }
+    return light_ok && p->steps >= 0 && p->max_step_vox > 0.0f && isfinite(p->k) && p->jitter_vox >= 0.0f &&
+           isfinite(p->jitter_vox);
 }
 
 }  // namespace

@@ -39,9 +39,10 @@ __device__ __forceinline__ void penumbra_step(Penumbra& p, float k, float d, flo
     }
 }
 
-__global__ void __launch_bounds__(256) k_shadow(ShadowArgs a, const float* __restrict__ sdf,
+__global__ void __launch_bounds__(256) k_shadow(ShadowArgs a_in, const float* __restrict__ sdf,
                                                 const float* __restrict__ pos, const float* __restrict__ nrm, int P,
                                                 float* __restrict__ vis) {
+    const ShadowArgs a = with_light(a_in);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const float3 o = march_origin(a, pos, nrm, i);
@@ -73,11 +74,12 @@ constexpr int kCoherentBlock = 512;  // receivers regrouped per block
 // runs on.  Each receiver's march is independent of the others, so the outputs are
 // those of k_shadow; steps[i] receives the new length (the step at which the march
 // stopped, at most 255).
-__global__ void __launch_bounds__(kCoherentBlock) k_shadow_coherent(ShadowArgs a, const float* __restrict__ sdf,
+__global__ void __launch_bounds__(kCoherentBlock) k_shadow_coherent(ShadowArgs a_in, const float* __restrict__ sdf,
                                                                     const float* __restrict__ pos,
                                                                     const float* __restrict__ nrm, int P,
                                                                     float* __restrict__ vis,
                                                                     uint8_t* __restrict__ steps) {
+    const ShadowArgs a = with_light(a_in);
     __shared__ uint32_t hist[256];
     __shared__ uint32_t wsum[8];
     __shared__ uint16_t perm[kCoherentBlock];

@@ -10,6 +10,7 @@ namespace rtsdf {
 struct ShadowArgs {
     GridD g;
     float3 L;  // unit direction toward the light (FP32, normalised on the host)
+    const float* Ldev;  // the caller's device light vector, or null (then L holds the direction)
     float k;
     int steps;
     float max_step, start_off, normal_off, hit_eps, bias;
@@ -20,9 +21,14 @@ struct ShadowArgs {
 inline ShadowArgs make_shadow_args(const rtsdf_grid& gh, const rtsdf_shadow_params& p) {
     ShadowArgs a;
     a.g = to_dev(gh);
-    const float* l = p.light_dir;
-    const float len = sqrtf(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
-    a.L = make_float3(l[0] / len, l[1] / len, l[2] / len);
+    a.Ldev = p.light_dir_device;
+    if (a.Ldev) {
+        a.L = make_float3(0.0f, 0.0f, 0.0f);  // resolved on the device (with_light)
+    } else {
+        const float* l = p.light_dir;
+        const float len = sqrtf(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+        a.L = make_float3(l[0] / len, l[1] / len, l[2] / len);
+    }
     a.k = p.k;
     a.steps = p.steps;
     a.max_step = p.max_step_vox;
@@ -33,6 +39,26 @@ inline ShadowArgs make_shadow_args(const rtsdf_grid& gh, const rtsdf_shadow_para
     a.jitter = p.jitter_vox;
     a.frame = p.frame_index;
     return a;
+}
+
+// Length of a light vector and its unit direction: the squared length summed x, y,
+// z, a correctly rounded square root and three correctly rounded divisions, the
+// same FP32 operations on the host (make_shadow_args) and on the device.
+__device__ __forceinline__ float3 unit_light(const float* __restrict__ l, float& len) {
+    const float l0 = __ldg(l), l1 = __ldg(l + 1), l2 = __ldg(l + 2);
+    len = sqrtf(l0 * l0 + l1 * l1 + l2 * l2);
+    return make_float3(l0 / len, l1 / len, l2 / len);
+}
+
+// The launch's arguments with the light direction resolved: from the caller's device
+// vector when one is given, else as normalised on the host.
+__device__ __forceinline__ ShadowArgs with_light(const ShadowArgs& a) {
+    ShadowArgs r = a;
+    if (a.Ldev) {
+        float len;
+        r.L = unit_light(a.Ldev, len);
+    }
+    return r;
 }
 
 // First sample distance of receiver i: start_off, moved along the light by a

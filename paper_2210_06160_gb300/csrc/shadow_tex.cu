@@ -17,9 +17,10 @@ struct rtsdf_texture {
 
 namespace rtsdf {
 
-__global__ void __launch_bounds__(256) k_shadow_tex(ShadowArgs a, cudaTextureObject_t tex,
+__global__ void __launch_bounds__(256) k_shadow_tex(ShadowArgs a_in, cudaTextureObject_t tex,
                                                     const float* __restrict__ pos, const float* __restrict__ nrm,
                                                     int P, float* __restrict__ vis) {
+    const ShadowArgs a = with_light(a_in);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const float3 o = march_origin(a, pos, nrm, i);
@@ -107,7 +108,9 @@ rtsdf_status rtsdf_shadow_tex(const rtsdf_texture* t, const float* pos, const fl
         return RTSDF_EINVAL;
     const float* l = p->light_dir;
     const float len2 = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
-    if (!(len2 > 0.0f) || p->steps < 0 || !(p->max_step_vox > 0.0f) || !(p->jitter_vox >= 0.0f)) return RTSDF_EINVAL;
+    const bool light_ok = p->light_dir_device ? reinterpret_cast<uintptr_t>(p->light_dir_device) % 4 == 0
+                                              : len2 > 0.0f;
+    if (!light_ok || p->steps < 0 || !(p->max_step_vox > 0.0f) || !(p->jitter_vox >= 0.0f)) return RTSDF_EINVAL;
     const ShadowArgs a = make_shadow_args(t->grid, *p);
     if (P == 0) return RTSDF_OK;
     k_shadow_tex<<<(P + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a, t->tex, pos, nrm, P, vis);

@@ -44,7 +44,7 @@ class ShadowParams(C.Structure):
     _fields_ = [("light_dir", C.c_float * 3), ("k", C.c_float), ("steps", C.c_int32),
                 ("max_step_vox", C.c_float), ("start_offset_vox", C.c_float),
                 ("normal_offset_vox", C.c_float), ("hit_eps_vox", C.c_float), ("bias_vox", C.c_float),
-                ("jitter_vox", C.c_float), ("frame_index", C.c_uint32)]
+                ("jitter_vox", C.c_float), ("frame_index", C.c_uint32), ("light_dir_device", C.c_void_p)]
 
 
 class Counters(C.Structure):
@@ -181,11 +181,20 @@ def make_refine_params(rp, count_work: bool = False) -> RefineParams:
                         float(getattr(rp, "decay_alpha", 0.95)), int(bool(count_work)))
 
 
-def make_shadow_params(sp) -> ShadowParams:
+def make_shadow_params(sp, light_device=None) -> ShadowParams:
+    """light_device: optional CUDA float32 tensor of 3 elements that the kernels read
+    for the light direction instead of sp.light_dir (the caller keeps it alive until
+    they have run)."""
+    ptr = None
+    if light_device is not None:
+        _dev(light_device, torch.float32, "light_device")
+        if light_device.numel() != 3:
+            raise RtsdfError("light_device must hold 3 floats")
+        ptr = C.c_void_p(light_device.data_ptr())
     return ShadowParams((C.c_float * 3)(*[float(v) for v in sp.light_dir]), float(sp.k), int(sp.steps),
                         float(sp.max_step_vox), float(sp.start_offset_vox), float(sp.normal_offset_vox),
                         float(sp.hit_eps_vox), float(sp.bias_vox), float(getattr(sp, "jitter_vox", 0.0)),
-                        int(getattr(sp, "frame_index", 0)) & 0xFFFFFFFF)
+                        int(getattr(sp, "frame_index", 0)) & 0xFFFFFFFF, ptr)
 
 
 # ------------------------------------------------------------ size queries
@@ -506,9 +515,11 @@ class SDFShadow(torch.autograd.Function):
     flood, then one tracked refine per entry of `frames`); differentiable in the
     vertices and the light direction through rtsdf_backward.
 
-    verts: CUDA float32 [V,3] world positions; light: float32 [3] tensor (any
-    device; its value parameterises the raymarch launch).  The backward must run
-    before `pipe` builds another field.
+    verts: CUDA float32 [V,3] world positions; light: float32 [3] tensor.  On the
+    GPU, the kernels read it where it lives (nothing is copied to the host, so a
+    forward and backward enqueue without synchronising); on the CPU its value
+    parameterises the launches.  The backward must run before `pipe` builds another
+    field.
     """
 
     @staticmethod
@@ -518,7 +529,12 @@ class SDFShadow(torch.autograd.Function):
         if int(shadow.steps) > BACKWARD_MAX_STEPS:
             raise RtsdfError(f"the adjoint replays at most {BACKWARD_MAX_STEPS} raymarch steps")
         import dataclasses
-        sp = dataclasses.replace(shadow, light_dir=tuple(float(v) for v in light.detach().cpu().tolist()))
+        light_dev = None
+        if light.is_cuda:
+            light_dev = light.detach().to(torch.float32).contiguous()
+            sp = shadow  # its light_dir is not read: the kernels take light_dev
+        else:
+            sp = dataclasses.replace(shadow, light_dir=tuple(float(v) for v in light.detach().tolist()))
         verts_c = verts.detach().contiguous()
         rparams = None
         for f, rp in enumerate(frames):
@@ -528,9 +544,10 @@ class SDFShadow(torch.autograd.Function):
             else:
                 pipe.refine(verts_c, tris, rparams)
         samples = pipe.sample(pts)
-        vis = pipe.shadow(pos, nrm, make_shadow_params(sp))
+        vis = pipe.shadow(pos, nrm, make_shadow_params(sp, light_dev))
         ctx.pipe, ctx.gen = pipe, pipe.generation
-        ctx.rparams, ctx.sparams = rparams, make_shadow_params(sp)
+        ctx.rparams, ctx.sparams = rparams, make_shadow_params(sp, light_dev)
+        ctx.light_dev = light_dev  # kept alive for the backward's launches
         ctx.tris, ctx.pts, ctx.pos, ctx.nrm = tris, pts, pos, nrm
         ctx.light_device = light.device
         ctx.save_for_backward(verts_c)

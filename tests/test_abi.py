@@ -120,6 +120,12 @@ def test_refine_and_shadow_parameter_validation(lib):
                                      None) == 1
     assert lib.rtsdf_shadow_coherent(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 4, C.byref(ok), P(FAKE), None,
                                      None) == 1
+    # a light read on the device: light_dir is then not looked at, the pointer must be 4-byte aligned
+    dev = ShadowParams((C.c_float * 3)(0, 0, 0), 8.0, 10, 1.0)
+    dev.light_dir_device = FAKE
+    assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 0, C.byref(dev), P(FAKE), None) == 0
+    dev.light_dir_device = FAKE + 2
+    assert lib.rtsdf_shadow(C.byref(g), P(FAKE), P(FAKE), P(FAKE), 0, C.byref(dev), P(FAKE), None) == 1
 
 
 def test_adjoint_entry_validation(lib):
@@ -247,21 +253,38 @@ def test_texture_entry_validation(lib):
     lib.rtsdf_texture_destroy(None)
 
 
+def _c_layout(tmp_path, ctype: str, fields) -> list[int]:
+    """sizeof and field offsets of a struct of include/rtsdf.h, as a C compiler lays it out."""
+    import subprocess
+    src = tmp_path / f"layout_{ctype}.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rtsdf.h"\nint main(void) {\n'
+                   f'    printf("%zu", sizeof({ctype}));\n'
+                   + "".join(f'    printf(" %zu", offsetof({ctype}, {f}));\n' for f in fields)
+                   + "    return 0;\n}\n")
+    exe = tmp_path / f"layout_{ctype}"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
+                           str(src), "-o", str(exe)])
+    return [int(v) for v in subprocess.check_output([str(exe)]).split()]
+
+
 def test_counters_layout_matches_the_header(tmp_path):
     """The binding's rtsdf_counters mirrors the C struct: size and field offsets as a
     C compiler lays out include/rtsdf.h."""
-    import subprocess
     from paper_2210_06160_gb300 import rtsdf
-    src = tmp_path / "layout.c"
     fields = [f for f, _ in rtsdf.Counters._fields_]
-    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rtsdf.h"\nint main(void) {\n'
-                   '    printf("%zu", sizeof(rtsdf_counters));\n'
-                   + "".join(f'    printf(" %zu", offsetof(rtsdf_counters, {f}));\n' for f in fields)
-                   + "    return 0;\n}\n")
-    exe = tmp_path / "layout"
-    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
-                           str(src), "-o", str(exe)])
-    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    got = _c_layout(tmp_path, "rtsdf_counters", fields)
     want = [C.sizeof(rtsdf.Counters)] + [getattr(rtsdf.Counters, f).offset for f in fields]
     assert got == want
     assert got[0] == 64 and rtsdf.COUNTER_WORDS == 16
+
+
+@pytest.mark.parametrize("name", ["ShadowParams", "RefineParams"])
+def test_parameter_structs_match_the_header(tmp_path, name):
+    """The binding's parameter structs mirror rtsdf_shadow_params and
+    rtsdf_refine_params field by field."""
+    from paper_2210_06160_gb300 import rtsdf
+    cls = getattr(rtsdf, name)
+    ctype = {"ShadowParams": "rtsdf_shadow_params", "RefineParams": "rtsdf_refine_params"}[name]
+    fields = [f for f, _ in cls._fields_]
+    got = _c_layout(tmp_path, ctype, fields)
+    assert got == [C.sizeof(cls)] + [getattr(cls, f).offset for f in fields]

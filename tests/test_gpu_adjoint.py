@@ -111,10 +111,10 @@ def _oracle_side(ds, light):
     return dict(r=r, src=src, s_tgt=s_tgt, v_tgt=v_tgt, loss=loss, gV=gV, gl=gl, samples=samples, vis=vis)
 
 
-def _gpu_side(ds, light, s_tgt, v_tgt):
+def _gpu_side(ds, light, s_tgt, v_tgt, light_on_gpu=False):
     sc = ds.scene
     verts = to_dev(sc.verts).requires_grad_(True)
-    L = torch.tensor(light, dtype=torch.float32, requires_grad=True)
+    L = torch.tensor(light, dtype=torch.float32, device="cuda" if light_on_gpu else "cpu", requires_grad=True)
     P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris), track=True)
     frames = [dataclasses.replace(sc.refine, frame_index=f, accumulate=int(sc.refine.accumulate) if f > 0 else 0)
               for f in range(sc.frames)]
@@ -124,12 +124,13 @@ def _gpu_side(ds, light, s_tgt, v_tgt):
     loss.backward()
     torch.cuda.synchronize()
     return dict(samples=samples.detach().cpu().numpy(), vis=vis.detach().cpu().numpy(), loss=float(loss.detach()),
-                gV=verts.grad.cpu().numpy().astype(np.float64), gl=L.grad.numpy().astype(np.float64))
+                gV=verts.grad.cpu().numpy().astype(np.float64), gl=L.grad.cpu().numpy().astype(np.float64),
+                gl_device=L.grad.device.type)
 
 
-def _compare(ds, light):
+def _compare(ds, light, light_on_gpu=False):
     o = _oracle_side(ds, light)
-    g = _gpu_side(ds, light, o["s_tgt"], o["v_tgt"])
+    g = _gpu_side(ds, light, o["s_tgt"], o["v_tgt"], light_on_gpu)
     np.testing.assert_array_equal(g["samples"], o["samples"])
     assert np.abs(g["vis"] - o["vis"]).max() <= 1e-4
     assert abs(g["loss"] - o["loss"]) <= 1e-4 * abs(o["loss"])
@@ -150,6 +151,20 @@ def test_adjoint_matches_fp64_oracle_miniature(jitter):
     ds = scenes.scene_diff(48, 2, 4, 1, n_samples=4096, shadow_res=64)
     sc = dataclasses.replace(ds.scene, shadow=dataclasses.replace(ds.scene.shadow, jitter_vox=jitter, frame_index=3))
     _compare(dataclasses.replace(ds, scene=sc), (0.3, 1.0, 0.2))
+
+
+def test_light_on_the_gpu_reads_the_same_direction():
+    """A light tensor on the GPU is read by the kernels where it lives (the C-ABI's
+    light_dir_device): the visibilities are bit-identical to those of the same light
+    given by value, the gradient meets the same FP64 bars and stays on the GPU."""
+    ds = scenes.scene_diff(48, 2, 4, 1, n_samples=4096, shadow_res=64)
+    light = (0.3, 1.0, 0.2)
+    o, g = _compare(ds, light, light_on_gpu=True)
+    assert g["gl_device"] == "cuda"
+    h = _gpu_side(ds, light, o["s_tgt"], o["v_tgt"], light_on_gpu=False)
+    np.testing.assert_array_equal(g["vis"], h["vis"])
+    np.testing.assert_array_equal(g["samples"], h["samples"])
+    assert np.abs(g["gl"] - h["gl"]).max() <= 1e-5 * max(np.abs(h["gl"]).max(), 1e-6)
 
 
 def test_adjoint_matches_fp64_oracle_128cube():
