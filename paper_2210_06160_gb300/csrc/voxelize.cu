@@ -3,12 +3,13 @@
 // Work decomposition: every valid triangle covers the bricks (8^3 voxels) of its
 // voxel range; a scan over the per-triangle brick counts turns the set of all
 // (triangle, brick) pairs into one virtual index space that warps stride over in
-// contiguous chunks (one binary search per chunk, no pair list, no host sync).
-// A warp first tests the triangle against the brick (slightly enlarged, so the
-// brick cull never rejects a voxel the voxel test accepts), then its lanes run
-// the voxel test on the voxels of (brick ∩ triangle range); an overlapping voxel
-// takes the 64-bit key (float bits of the closest-point distance^2, triangle id)
-// with atomicMin, which is the argmin with ties to the lower id in any order.
+// contiguous chunks of 32 items (one binary search per chunk, no pair list, no host
+// sync).  Each lane takes one item of the chunk: it tests its triangle against its
+// brick (slightly enlarged, so the brick cull never rejects a voxel the voxel test
+// accepts), and the voxel tests of the chunk's items on (brick ∩ triangle range)
+// are then spread over the lanes (vox_chunk); an overlapping voxel takes the 64-bit
+// key (float bits of the closest-point distance^2, triangle id) with atomicMin,
+// which is the argmin with ties to the lower id in any order.
 #include "rtsdf_launch.cuh"
 #include "voxelize_core.cuh"
 
