@@ -33,7 +33,7 @@ METRIC = "SDF rebuild ms/frame @400x200x400, GVoxel/s, %HBM roof; bwd+batch vs p
 # room frame, from one ncu capture, with the SHA-256 (first 16 hex digits) of the code of the
 # flooding sources it was taken on (comments stripped); the bench reports it only while that
 # code is unchanged
-JFA_ROOM_TRAFFIC = {"bytes_per_frame": 2_213_477_632, "sources_sha256_16": "66476ffb57ce1891"}
+JFA_ROOM_TRAFFIC = {"bytes_per_frame": 2_211_134_720, "sources_sha256_16": "13f05a812ff87b66"}
 JFA_SOURCES = ("paper_2210_06160_gb300/csrc/jfa_core.cuh", "paper_2210_06160_gb300/csrc/jfa.cu")
 # algorithmic operations per unit of refinement work (counted by the kernel in rtsdf_counters):
 # a ray is a Philox4x32-10 draw and Marsaglia's direction (about 20 FP32 and 40 integer

@@ -31,7 +31,7 @@ rtsdf_status jfa(const rtsdf_grid& g, int32_t* a, int32_t* b, const int32_t* ste
         const bool pow2 = k >= 64 && k <= 256 && (k & (k - 1)) == 0;
         const unsigned gx = (unsigned)jfa_xblocks(g.nx, k), gy = (unsigned)((g.ny + kJY - 1) / kJY);
         if (pow2 && nq <= kGroupMaxPlanes) {
-            const int grp = kChunk / nq;
+            const int grp = kGroupOutputs / nq;
             const dim3 grid(gx, gy, (unsigned)((k + grp - 1) / grp));
             if (k == 64)
                 k_jfa_pass_grouped<64><<<grid, block, 0, s>>>(src, dst, g.nx, g.ny, g.nz, grp);

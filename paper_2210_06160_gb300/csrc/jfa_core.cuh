@@ -13,9 +13,10 @@
 namespace rtsdf {
 
 constexpr int kJX = 32, kJY = 4;  // block of columns (x, y)
-constexpr int kChunk = 32;        // outputs per column and block along z (grids of 16 M voxels and more)
+constexpr int kChunk = 64;        // outputs per column and block along z (grids of 16 M voxels and more)
 constexpr int kChunkSmall = 16;   // the same for smaller grids, which need more threads to fill the GPU
-constexpr int kGroupMaxPlanes = kChunk / 2;  // classes this short are grouped per thread
+constexpr int kGroupMaxPlanes = 16;  // classes this short are grouped per thread
+constexpr int kGroupOutputs = 32;    // outputs a thread of the grouped passes takes (whole classes)
 
 __host__ __device__ __forceinline__ int jfa_xblocks(int nx, int /*k*/) { return (nx + kJX - 1) / kJX; }
 
@@ -298,7 +299,7 @@ __device__ __forceinline__ void jfa_column(const uint32_t* __restrict__ in, uint
 
 // Large offsets (every residue class holds at most kGroupMaxPlanes planes): one
 // thread takes grp consecutive classes of its column, so its fixed costs are spread
-// over about kChunk outputs.  Its own kernel, so the loop does not weigh on the
+// over about kGroupOutputs outputs.  Its own kernel, so the loop does not weigh on the
 // register allocation of the common path.
 template <int K>
 __device__ __forceinline__ void jfa_column_grouped(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
