@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ Bat
                              (int32_t)(si << kBrickBits), smask);
 }
 
-template <int BX, int BY, int BZ, int RPL>
+template <int BX, int BY, int BZ, int RPL, bool kCull>
 __global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t,
                                                                   const __grid_constant__ RefineTable R, BatchGrids G,
                                                                   const char* __restrict__ bvh,
@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() 
         const int n_inner = n_leaves > 1 ? n_leaves - 1 : 1;
         const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
         const int64_t o = S.vox_off;
-        refine_brick<BX, BY, BZ, false, RPL>(a, nodes, leaves, n_leaves, n_inner, (S.flood_b ? G.buf_b : G.buf_a) + o,
+        refine_brick<BX, BY, BZ, false, RPL, false, kCull>(a, nodes, leaves, n_leaves, n_inner,
+                                                          (S.flood_b ? G.buf_b : G.buf_a) + o,
                                         G.rep_tri + o, bmask[S.brick_off + b], bx, by, bz, G.dist_bits + o,
                                         G.front + o, G.back + o, G.sdf + o, nullptr, nullptr, w, n_hit, n_fail,
                                         n_ovf);
@@ -528,7 +529,7 @@ rtsdf_status run_jfa(rtsdf_batch_plan& P, uint32_t* a, uint32_t* b, cudaStream_t
     return RTSDF_OK;
 }
 
-template <int BX, int BY, int BZ, int RPL>
+template <int BX, int BY, int BZ, int RPL, bool kCull>
 rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers& B, uint32_t frame, int accumulate,
                            rtsdf_counters* counters, int warps, cudaStream_t s) {
     const Shape sh{BX, BY, BZ};
@@ -551,12 +552,12 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ, RPL, kCull>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(sizeof(WarpSmemT<RPL>) * 4)));
         attr_set[dev] = true;
     }
     // the same resident warps per SM for every CTA size (shared memory bound)
-    k_brefine<BX, BY, BZ, RPL><<<num_sms() * (refine_warps_per_sm<RPL>() / warps), 32 * warps, smem, s>>>(t, R, G,
+    k_brefine<BX, BY, BZ, RPL, kCull><<<num_sms() * (refine_warps_per_sm<RPL>() / warps), 32 * warps, smem, s>>>(t, R, G,
                                                                             static_cast<const char*>(B.bvh), bmask,
                                                                             blist, count, counters);
     RTSDF_LAUNCHED();
@@ -575,8 +576,15 @@ rtsdf_status refine_step(const rtsdf_batch_plan& P, const rtsdf_batch_buffers& B
     int rmax = 1;  // one ray group per brick for up to rpl rays (the largest ray count of the batch)
     for (const rtsdf_batch_scene& sc : P.scenes) rmax = sc.refine.rays_per_voxel > rmax ? sc.refine.rays_per_voxel : rmax;
     const int rpl = rmax <= 2 ? 2 : (rmax <= 4 ? 4 : (rmax <= 8 ? 8 : 16));
-#define RTSDF_BATCH_CASE(X, Y, Z, R) \
-    if (tu.brick_x == X && rpl == R) return launch_refine<X, Y, Z, R>(P, B, frame, accumulate, counters, w, s);
+    // the culling instantiation when some scene is coarse (many triangles within a brick's reach)
+    bool cull = false;
+    for (const rtsdf_batch_scene& sc : P.scenes)
+        cull = cull || staged_estimate(sc.T, sc.grid.nx, sc.grid.ny, sc.grid.nz, sc.refine.max_ray_vox, tu.brick_x,
+                                       tu.brick_y, tu.brick_z) >= kCullEstimate;
+#define RTSDF_BATCH_CASE(X, Y, Z, R)                                                                  \
+    if (tu.brick_x == X && rpl == R)                                                                  \
+        return cull ? launch_refine<X, Y, Z, R, true>(P, B, frame, accumulate, counters, w, s)        \
+                    : launch_refine<X, Y, Z, R, false>(P, B, frame, accumulate, counters, w, s);
     RTSDF_BATCH_CASE(4, 4, 4, 2) RTSDF_BATCH_CASE(4, 4, 4, 4) RTSDF_BATCH_CASE(4, 4, 4, 8)
     RTSDF_BATCH_CASE(4, 4, 4, 16)
     RTSDF_BATCH_CASE(8, 4, 2, 2) RTSDF_BATCH_CASE(8, 4, 2, 4) RTSDF_BATCH_CASE(8, 4, 2, 8)

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(512, 4) k_resolve(RefineArgs a, const int32_t*
 // ------------------------------------------------------------------ refine
 
 // Persistent: warps take bricks from the work list until it is exhausted.
-template <bool kTrack, int RPL, bool kCount>
+template <bool kTrack, int RPL, bool kCount, bool kCull>
 __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 32 / kRefineThreads) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 3
         if (wk >= nact) break;
         const int b = blist[wk];
         const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
-        refine_brick<kBX, kBY, kBZ, kTrack, RPL, kCount>(a, nodes, leaves, n_leaves, n_inner, nearest, rep_tri, bmask[b], bx, by,
+        refine_brick<kBX, kBY, kBZ, kTrack, RPL, kCount, kCull>(a, nodes, leaves, n_leaves, n_inner, nearest, rep_tri, bmask[b], bx, by,
                                             bz, dist_bits, front, back, sdf, win_ray, win_tri, w, n_hit, n_fail,
                                             n_ovf);
     }
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 3
     if (lane == 0 && n_ovf) atomicAdd(count + 2, n_ovf);
 }
 
-template <bool kTrack, int RPL, bool kCount>
+template <bool kTrack, int RPL, bool kCount, bool kCull>
 static rtsdf_status launch_refine_t(cudaStream_t s, const RefineArgs& a, const BvhHeader* hdr,
                                     const BvhNode* nodes, const BvhLeaf* leaves, const int32_t* nearest,
                                     const int32_t* rep_tri, const unsigned long long* bmask, const int32_t* blist,
@@ -130,31 +130,37 @@ static rtsdf_status launch_refine_t(cudaStream_t s, const RefineArgs& a, const B
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RTSDF_CUDA(cudaFuncSetAttribute(k_refine<kTrack, RPL, kCount>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        RTSDF_CUDA(cudaFuncSetAttribute(k_refine<kTrack, RPL, kCount, kCull>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
         attr_set[dev] = true;
     }
-    k_refine<kTrack, RPL, kCount><<<num_sms() * (refine_warps_per_sm<RPL>() * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
+    k_refine<kTrack, RPL, kCount, kCull><<<num_sms() * (refine_warps_per_sm<RPL>() * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
         a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count, dist_bits, front, back, sdf, counters, win_ray,
         win_tri);
     return RTSDF_OK;
 }
 
-static rtsdf_status launch_refine_kernel(bool track, bool count, int rpl, cudaStream_t s, const RefineArgs& a,
-                                         const BvhHeader* hdr, const BvhNode* nodes, const BvhLeaf* leaves,
-                                         const int32_t* nearest, const int32_t* rep_tri,
+static rtsdf_status launch_refine_kernel(bool track, bool count, bool cull, int rpl, cudaStream_t s,
+                                         const RefineArgs& a, const BvhHeader* hdr, const BvhNode* nodes,
+                                         const BvhLeaf* leaves, const int32_t* nearest, const int32_t* rep_tri,
                                          const unsigned long long* bmask, const int32_t* blist, uint32_t* wcount,
                                          uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
                                          rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
-#define RTSDF_REFINE_CASE(T, R, N)                                                                              \
-    if (track == T && rpl == R && count == N)                                                                   \
-        return launch_refine_t<T, R, N>(s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, wcount,       \
-                                        dist_bits, front, back, sdf, counters, T ? win_ray : nullptr,           \
-                                        T ? win_tri : nullptr);
-    RTSDF_REFINE_CASE(false, 2, false) RTSDF_REFINE_CASE(false, 4, false) RTSDF_REFINE_CASE(false, 8, false)
-    RTSDF_REFINE_CASE(false, 16, false) RTSDF_REFINE_CASE(true, 2, false) RTSDF_REFINE_CASE(true, 4, false)
-    RTSDF_REFINE_CASE(true, 8, false) RTSDF_REFINE_CASE(true, 16, false) RTSDF_REFINE_CASE(false, 2, true)
-    RTSDF_REFINE_CASE(false, 4, true) RTSDF_REFINE_CASE(false, 8, true) RTSDF_REFINE_CASE(false, 16, true)
+#define RTSDF_REFINE_CASE(T, R, N, C)                                                                           \
+    if (track == T && rpl == R && count == N && cull == C)                                                      \
+        return launch_refine_t<T, R, N, C>(s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, wcount,    \
+                                           dist_bits, front, back, sdf, counters, T ? win_ray : nullptr,        \
+                                           T ? win_tri : nullptr);
+    RTSDF_REFINE_CASE(false, 2, false, false) RTSDF_REFINE_CASE(false, 4, false, false)
+    RTSDF_REFINE_CASE(false, 8, false, false) RTSDF_REFINE_CASE(false, 16, false, false)
+    RTSDF_REFINE_CASE(true, 2, false, false) RTSDF_REFINE_CASE(true, 4, false, false)
+    RTSDF_REFINE_CASE(true, 8, false, false) RTSDF_REFINE_CASE(true, 16, false, false)
+    RTSDF_REFINE_CASE(false, 2, true, false) RTSDF_REFINE_CASE(false, 4, true, false)
+    RTSDF_REFINE_CASE(false, 8, true, false) RTSDF_REFINE_CASE(false, 16, true, false)
+    RTSDF_REFINE_CASE(false, 2, false, true) RTSDF_REFINE_CASE(false, 4, false, true)
+    RTSDF_REFINE_CASE(false, 8, false, true) RTSDF_REFINE_CASE(false, 16, false, true)
+    RTSDF_REFINE_CASE(false, 2, true, true) RTSDF_REFINE_CASE(false, 4, true, true)
+    RTSDF_REFINE_CASE(false, 8, true, true) RTSDF_REFINE_CASE(false, 16, true, true)
 #undef RTSDF_REFINE_CASE
     return RTSDF_EINVAL;
 }
@@ -212,7 +218,10 @@ rtsdf_status refine(const rtsdf_grid& gh, int32_t T, const void* bvh, const int3
     const int rpl = a.R <= 2 ? 2 : (a.R <= 4 ? 4 : (a.R <= 8 ? 8 : 16));  // one ray group for up to rpl rays
     // work counting: only untracked calls that pass counters and ask for it
     const bool count_work = !track && counters != nullptr && p.count_work != 0;
-    RTSDF_TRY(launch_refine_kernel(track, count_work, rpl, s, a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
+    // coarse grids (many triangles within a brick's reach) take the culling instantiation;
+    // tracked calls (the adjoint's forward) keep the plain one
+    const bool cull = !track && staged_estimate(T, gh.nx, gh.ny, gh.nz, a.tmax, kBX, kBY, kBZ) >= kCullEstimate;
+    RTSDF_TRY(launch_refine_kernel(track, count_work, cull, rpl, s, a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
                                    w.count, dist_bits, front, back, sdf, counters, win_ray, win_tri));
     RTSDF_LAUNCHED();
     if (counters) {

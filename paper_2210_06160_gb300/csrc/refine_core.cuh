@@ -15,6 +15,21 @@ constexpr int kListCap = 256;        // staged leaves per warp and round
 constexpr int kStackCapW = 256;      // traversal stack per warp (entries)
 constexpr int kNarrowMargin = 96;    // > depth of any tree the builder makes (30-bit codes + 32 index bits)
 constexpr int kRaysPerLane = 8;      // rays of a voxel per group for up to 8 rays (one lane per voxel)
+constexpr int kCullMinStaged = 160;  // staged triangles from which a brick culls (voxel, chunk) combinations
+constexpr double kCullEstimate = 150.0;  // staged_estimate from which a launch takes the culling instantiation
+
+// Triangles a brick of BX x BY x BZ voxels would stage if the mesh filled the grid
+// evenly: T times the fraction of the grid its reach box (grown by the ray length)
+// covers.  A coarse grid, whose ray length spans much of the scene, scores in the
+// hundreds or thousands (the 400x200x400 room: 27; a 32^3 grid with 50 k triangles:
+// 12 k).  Launches above kCullEstimate take the instantiation that culls (voxel,
+// chunk) combinations (chunk_voxels); the others keep the plain loop, whose code
+// runs faster when no brick stages that many triangles.
+inline double staged_estimate(int T, int nx, int ny, int nz, float tmax, int bx, int by, int bz) {
+    const double e = 2.0 * (double)tmax;
+    const double f = ((double)bx + e) * ((double)by + e) * ((double)bz + e) / ((double)nx * ny * nz);
+    return (double)T * (f < 1.0 ? f : 1.0);
+}
 constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
 constexpr int kRefineWarpsPerSm = 20;                 // resident refine warps per SM (shared memory bound)
 constexpr int kRefineWarpsPerSm16 = 12;               // the same with 16-ray groups (twice the ray rows)
@@ -449,6 +464,65 @@ __device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int b
     __syncwarp();
 }
 
+// Order-preserving map between FP32 values and signed integers (an involution), so
+// that warp integer reductions give float minima and maxima.
+__device__ __forceinline__ int f2ord(float f) {
+    const int k = __float_as_int(f);
+    return k ^ ((k >> 31) & 0x7FFFFFFF);
+}
+__device__ __forceinline__ float ord2f(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7FFFFFFF)); }
+
+// Voxel slots of the pass (bit v, v < nv) with a ray that can reach a triangle of the
+// staged chunk: a sphere around the box of the chunk's bounding spheres (lane j holds
+// triangle j's sphere, valid when `have`), grown by a margin above FP32 rounding, is
+// tested like a triangle's in filter_pair: out of reach of the voxel, or missed by the
+// line of every ray, means no triangle of the chunk can be hit from that voxel.  On
+// coarse grids, where a brick stages thousands of triangles within reach of its voxels,
+// most (voxel, chunk) combinations fail and their pairs are never formed.
+template <int RPL>
+__device__ __forceinline__ uint32_t chunk_voxels(const WarpSmemT<RPL>& w, float4 sph, bool have, int nv,
+                                                 float tmax) {
+    constexpr int kQ = (RPL + 3) / 4;
+    const int lane = threadIdx.x & 31;
+    const int big = 0x7FFFFFFF, small = (int)0x80000000;
+    const float3 lo = make_float3(ord2f(__reduce_min_sync(0xffffffffu, have ? f2ord(sph.x - sph.w) : big)),
+                                  ord2f(__reduce_min_sync(0xffffffffu, have ? f2ord(sph.y - sph.w) : big)),
+                                  ord2f(__reduce_min_sync(0xffffffffu, have ? f2ord(sph.z - sph.w) : big)));
+    const float3 hi = make_float3(ord2f(__reduce_max_sync(0xffffffffu, have ? f2ord(sph.x + sph.w) : small)),
+                                  ord2f(__reduce_max_sync(0xffffffffu, have ? f2ord(sph.y + sph.w) : small)),
+                                  ord2f(__reduce_max_sync(0xffffffffu, have ? f2ord(sph.z + sph.w) : small)));
+    const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+    const float hx = hi.x - lo.x, hy = hi.y - lo.y, hz = hi.z - lo.z;
+    const float rho = 0.5f * sqrtf(__fmaf_rn(hx, hx, __fmaf_rn(hy, hy, hz * hz))) * 1.00001f + 1e-3f;
+    const float4 o = w.origin[lane];
+    const float dcx = cx - o.x, dcy = cy - o.y, dcz = cz - o.z;
+    const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
+    const float reach = rho + tmax * 1.00001f + 1e-3f;
+    bool pass = lane < nv && dd <= reach * reach;
+    if (pass) {
+        const float rho2 = rho * rho;
+        const float v2 = dd - rho2;
+        const float thr = v2 > rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho * 1.000001f - 1e-4f;
+        const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
+        const float2 nthr2 = make_float2(-thr, -thr);
+        uint32_t any = 0;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const float4 qx = w.dq[0][q][lane], qy = w.dq[1][q][lane], qz = w.dq[2][q][lane];
+            const float2 t0 = __ffma2_rn(cx2, make_float2(qx.x, qx.y),
+                                         __ffma2_rn(cy2, make_float2(qy.x, qy.y),
+                                                    __ffma2_rn(cz2, make_float2(qz.x, qz.y), nthr2)));
+            const float2 t1 = __ffma2_rn(cx2, make_float2(qx.z, qx.w),
+                                         __ffma2_rn(cy2, make_float2(qy.z, qy.w),
+                                                    __ffma2_rn(cz2, make_float2(qz.z, qz.w), nthr2)));
+            // a ray passes when its result is non-negative: some sign bit clear
+            any |= ~(__float_as_uint(t0.x) & __float_as_uint(t0.y) & __float_as_uint(t1.x) & __float_as_uint(t1.y));
+        }
+        pass = (any >> 31) != 0u;
+    }
+    return __ballot_sync(0xffffffffu, pass);
+}
+
 // Position of the n-th set bit (from 0) of m, n < popc(m): a binary search on
 // population counts, the same few steps in every lane.
 __device__ __forceinline__ int nth_set_bit(unsigned long long m, int n) {
@@ -534,7 +608,7 @@ __device__ __forceinline__ void redraw(WarpSmemT<RPL>& w, uint32_t need, const R
 // multiply-adds because they decide nothing the oracle decides.
 // RPL: rays per lane and group (2, 4 or 8); calls with R <= RPL rays per voxel run
 // one group, so small ray counts do not pay for eight.
-template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane, bool kCount = false>
+template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane, bool kCount = false, bool kCull = false>
 __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode* __restrict__ nodes,
                                              const BvhLeaf* __restrict__ leaves, int n_leaves, int n_inner,
                                              const int32_t* __restrict__ nearest,
@@ -659,9 +733,15 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                         reach2 = reach * reach;
                     }
                     __syncwarp();
+                    // the chunk's voxels: with kCull, on bricks that stage many triangles, those
+                    // with a ray that can reach any triangle of the chunk; else all of them
+                    const uint32_t vsel = kCull && nc >= kCullMinStaged
+                                              ? chunk_voxels<RPL>(w, sph, c < nc, nv, a.tmax)
+                                              : 0xffffffffu;
                     int np = 0;
                     const uint32_t lt = (1u << lane) - 1u;
                     for (int v0 = 0; v0 < nv; v0 += 4) {
+                        if (((vsel >> v0) & 0xFu) == 0u) continue;  // four culled voxels (warp-uniform)
                         bool ok[4];
                         uint32_t b[4];
 #pragma unroll
@@ -670,7 +750,7 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                             const float4 ov = w.origin[v & 31];
                             const float dcx = sph.x - ov.x, dcy = sph.y - ov.y, dcz = sph.z - ov.z;
                             const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
-                            ok[e] = v < nv && dd <= reach2;
+                            ok[e] = v < nv && ((vsel >> (v & 31)) & 1u) && dd <= reach2;
                             b[e] = __ballot_sync(0xffffffffu, ok[e]);
                         }
 #pragma unroll

@@ -47,6 +47,18 @@ def test_small_room_accumulated_frames_parity():
     assert np.abs(vis - vis_ref).max() <= SHADOW_TOL
 
 
+def test_coarse_grid_parity():
+    """The small room on a 24x12x24 grid: the 8-voxel rays span a third of the scene,
+    so every brick stages most of the mesh and the refinement takes its culling form
+    (whole chunks of staged triangles skipped for voxels whose rays miss their
+    bounding sphere); the field must still equal the oracle's, whole grid, two
+    accumulated frames."""
+    sc = scenes.scene_small_room(n=24)
+    ref = oracle.rebuild(sc)
+    got, _ = gpu_rebuild(sc)
+    compare_rebuild(ref, got)
+
+
 def _random_scene(seed=0, dims=(37, 21, 29), n=60, R=5):
     rng = np.random.default_rng(seed)
     g = scenes.Grid(*dims, (-0.3, 0.1, -0.2), 0.05)
