@@ -464,63 +464,76 @@ __device__ __forceinline__ void filter_and_queue(WarpSmemT<RPL>& w, int n, int b
     __syncwarp();
 }
 
-// Order-preserving map between FP32 values and signed integers (an involution), so
-// that warp integer reductions give float minima and maxima.
-__device__ __forceinline__ int f2ord(float f) {
-    const int k = __float_as_int(f);
-    return k ^ ((k >> 31) & 0x7FFFFFFF);
-}
-__device__ __forceinline__ float ord2f(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7FFFFFFF)); }
-
-// Voxel slots of the pass (bit v, v < nv) with a ray that can reach a triangle of the
-// staged chunk: a sphere around the box of the chunk's bounding spheres (lane j holds
-// triangle j's sphere, valid when `have`), grown by a margin above FP32 rounding, is
-// tested like a triangle's in filter_pair: out of reach of the voxel, or missed by the
-// line of every ray, means no triangle of the chunk can be hit from that voxel.  On
-// coarse grids, where a brick stages thousands of triangles within reach of its voxels,
-// most (voxel, chunk) combinations fail and their pairs are never formed.
+// (Voxel, triangle group) combinations of a staged chunk that can produce a hit.  The
+// chunk's four groups of 8 triangles (lanes 8g .. 8g + 7, lane j holding triangle j's
+// bounding sphere, valid when `have`) each get a sphere around the box of their
+// triangles' spheres, grown by a margin above FP32 rounding; every voxel of the pass
+// (lane v < nv) tests its rays against the four like a triangle's sphere in
+// filter_pair: a group out of the voxel's reach, or whose sphere every ray line
+// misses, holds no triangle any of the voxel's rays can hit.  Returns the voxels with
+// some group left (bit v) and sets, in lane v, the 4-bit mask of its groups (bit g);
+// the voxel's pairs are formed with those groups' triangles only.  On coarse grids,
+// where a brick stages thousands of triangles within reach of its voxels, most
+// combinations fail and their pairs are never formed.
 template <int RPL>
 __device__ __forceinline__ uint32_t chunk_voxels(const WarpSmemT<RPL>& w, float4 sph, bool have, int nv,
-                                                 float tmax) {
+                                                  float tmax, uint32_t& groups) {
     constexpr int kQ = (RPL + 3) / 4;
     const int lane = threadIdx.x & 31;
-    const int big = 0x7FFFFFFF, small = (int)0x80000000;
-    const float3 lo = make_float3(ord2f(__reduce_min_sync(0xffffffffu, have ? f2ord(sph.x - sph.w) : big)),
-                                  ord2f(__reduce_min_sync(0xffffffffu, have ? f2ord(sph.y - sph.w) : big)),
-                                  ord2f(__reduce_min_sync(0xffffffffu, have ? f2ord(sph.z - sph.w) : big)));
-    const float3 hi = make_float3(ord2f(__reduce_max_sync(0xffffffffu, have ? f2ord(sph.x + sph.w) : small)),
-                                  ord2f(__reduce_max_sync(0xffffffffu, have ? f2ord(sph.y + sph.w) : small)),
-                                  ord2f(__reduce_max_sync(0xffffffffu, have ? f2ord(sph.z + sph.w) : small)));
-    const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
-    const float hx = hi.x - lo.x, hy = hi.y - lo.y, hz = hi.z - lo.z;
-    const float rho = 0.5f * sqrtf(__fmaf_rn(hx, hx, __fmaf_rn(hy, hy, hz * hz))) * 1.00001f + 1e-3f;
-    const float4 o = w.origin[lane];
-    const float dcx = cx - o.x, dcy = cy - o.y, dcz = cz - o.z;
-    const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
-    const float reach = rho + tmax * 1.00001f + 1e-3f;
-    bool pass = lane < nv && dd <= reach * reach;
-    if (pass) {
-        const float rho2 = rho * rho;
-        const float v2 = dd - rho2;
-        const float thr = v2 > rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho * 1.000001f - 1e-4f;
-        const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
-        const float2 nthr2 = make_float2(-thr, -thr);
-        uint32_t any = 0;
+    const float inf = __int_as_float(0x7f800000);
+    float lx = have ? sph.x - sph.w : inf, ly = have ? sph.y - sph.w : inf, lz = have ? sph.z - sph.w : inf;
+    float hx = have ? sph.x + sph.w : -inf, hy = have ? sph.y + sph.w : -inf, hz = have ? sph.z + sph.w : -inf;
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            const float4 qx = w.dq[0][q][lane], qy = w.dq[1][q][lane], qz = w.dq[2][q][lane];
-            const float2 t0 = __ffma2_rn(cx2, make_float2(qx.x, qx.y),
-                                         __ffma2_rn(cy2, make_float2(qy.x, qy.y),
-                                                    __ffma2_rn(cz2, make_float2(qz.x, qz.y), nthr2)));
-            const float2 t1 = __ffma2_rn(cx2, make_float2(qx.z, qx.w),
-                                         __ffma2_rn(cy2, make_float2(qy.z, qy.w),
-                                                    __ffma2_rn(cz2, make_float2(qz.z, qz.w), nthr2)));
-            // a ray passes when its result is non-negative: some sign bit clear
-            any |= ~(__float_as_uint(t0.x) & __float_as_uint(t0.y) & __float_as_uint(t1.x) & __float_as_uint(t1.y));
-        }
-        pass = (any >> 31) != 0u;
+    for (int off = 1; off < 8; off <<= 1) {  // within each group of 8 lanes
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, off));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, off));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, off));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, off));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, off));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, off));
     }
-    return __ballot_sync(0xffffffffu, pass);
+    const bool gvalid = lx <= hx;  // the group holds a staged triangle
+    const float gx = 0.5f * (lx + hx), gy = 0.5f * (ly + hy), gz = 0.5f * (lz + hz);
+    const float ex = hx - lx, ey = hy - ly, ez = hz - lz;
+    const float grho =
+        gvalid ? 0.5f * sqrtf(__fmaf_rn(ex, ex, __fmaf_rn(ey, ey, ez * ez))) * 1.00001f + 1e-3f : 0.0f;
+    const float4 o = w.origin[lane];
+    const bool mine = lane < nv;
+    uint32_t m = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const float cx = __shfl_sync(0xffffffffu, gx, 8 * g), cy = __shfl_sync(0xffffffffu, gy, 8 * g),
+                    cz = __shfl_sync(0xffffffffu, gz, 8 * g), rho = __shfl_sync(0xffffffffu, grho, 8 * g);
+        const bool valid = __shfl_sync(0xffffffffu, gvalid, 8 * g);
+        const float dcx = cx - o.x, dcy = cy - o.y, dcz = cz - o.z;
+        const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
+        const float reach = rho + tmax * 1.00001f + 1e-3f;
+        bool pass = mine && valid && dd <= reach * reach;
+        if (pass) {
+            const float rho2 = rho * rho;
+            const float v2 = dd - rho2;
+            const float thr = v2 > rho2 ? (v2 * rsqrtf(v2)) * 0.999999f - 1e-4f : -rho * 1.000001f - 1e-4f;
+            const float2 cx2 = make_float2(dcx, dcx), cy2 = make_float2(dcy, dcy), cz2 = make_float2(dcz, dcz);
+            const float2 nthr2 = make_float2(-thr, -thr);
+            uint32_t any = 0;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const float4 qx = w.dq[0][q][lane], qy = w.dq[1][q][lane], qz = w.dq[2][q][lane];
+                const float2 t0 = __ffma2_rn(cx2, make_float2(qx.x, qx.y),
+                                             __ffma2_rn(cy2, make_float2(qy.x, qy.y),
+                                                        __ffma2_rn(cz2, make_float2(qz.x, qz.y), nthr2)));
+                const float2 t1 = __ffma2_rn(cx2, make_float2(qx.z, qx.w),
+                                             __ffma2_rn(cy2, make_float2(qy.z, qy.w),
+                                                        __ffma2_rn(cz2, make_float2(qz.z, qz.w), nthr2)));
+                any |= ~(__float_as_uint(t0.x) & __float_as_uint(t0.y) & __float_as_uint(t1.x) &
+                         __float_as_uint(t1.y));
+            }
+            pass = (any >> 31) != 0u;
+        }
+        m |= pass ? 1u << g : 0u;
+    }
+    groups = m;
+    return __ballot_sync(0xffffffffu, m != 0u);
 }
 
 // Position of the n-th set bit (from 0) of m, n < popc(m): a binary search on
@@ -735,8 +748,9 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                     __syncwarp();
                     // the chunk's voxels: with kCull, on bricks that stage many triangles, those
                     // with a ray that can reach any triangle of the chunk; else all of them
+                    uint32_t groups = 0xFu;  // lane v: the triangle groups voxel v is paired with
                     const uint32_t vsel = kCull && nc >= kCullMinStaged
-                                              ? chunk_voxels<RPL>(w, sph, c < nc, nv, a.tmax)
+                                              ? chunk_voxels<RPL>(w, sph, c < nc, nv, a.tmax, groups)
                                               : 0xffffffffu;
                     int np = 0;
                     const uint32_t lt = (1u << lane) - 1u;
@@ -750,7 +764,9 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
                             const float4 ov = w.origin[v & 31];
                             const float dcx = sph.x - ov.x, dcy = sph.y - ov.y, dcz = sph.z - ov.z;
                             const float dd = __fmaf_rn(dcx, dcx, __fmaf_rn(dcy, dcy, dcz * dcz));
-                            ok[e] = v < nv && ((vsel >> (v & 31)) & 1u) && dd <= reach2;
+                            const uint32_t gv = kCull ? __shfl_sync(0xffffffffu, groups, v & 31) : 0xFu;
+                            ok[e] = v < nv && ((vsel >> (v & 31)) & 1u) && ((gv >> (lane >> 3)) & 1u) &&
+                                    dd <= reach2;
                             b[e] = __ballot_sync(0xffffffffu, ok[e]);
                         }
 #pragma unroll
