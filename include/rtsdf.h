@@ -102,7 +102,8 @@ typedef struct {
 /* Device-side counters; each call adds to the fields it owns.  The caller zeroes
  * the block and reads it back; it must be 8-byte aligned.  The 64-bit fields count
  * the refinement's work (Sec. 2.1), for throughput figures:
- *   node_tests   BVH child boxes tested against a brick's reach region,
+ *   node_tests   BVH child boxes tested against a brick's reach region (or, for the
+ *                bricks of a coarse grid that walk each ray on its own, against a ray),
  *   reach_tests  (masked voxel, staged triangle) pairs tested for reach,
  *   filter_pairs pairs within reach, each then filtered against every ray of the voxel,
  *   exact_tests  (ray, triangle) pairs given the exact Moller-Trumbore test.

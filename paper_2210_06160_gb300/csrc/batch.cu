@@ -253,6 +253,7 @@ __host__ __device__ inline RefineArgs scene_args(const SceneD& S, const char* bv
     a.nbx = (S.g.nx + BX - 1) / BX;
     a.nby = (S.g.ny + BY - 1) / BY;
     a.nbz = (S.g.nz + BZ - 1) / BZ;
+    a.per_ray = 0;
     return a;
 }
 
@@ -299,25 +300,29 @@ __global__ void __launch_bounds__(512, 4) k_bresolve(const __grid_constant__ Bat
                              (int32_t)(si << kBrickBits), smask);
 }
 
-template <int BX, int BY, int BZ, int RPL, bool kCull>
+// Persistent, like k_refine: with kCull the bricks that refine_brick leaves to the
+// per-ray launch go to dlist (as their work-list entries); with kRays the kernel is
+// that launch and takes its bricks from dlist.
+template <int BX, int BY, int BZ, int RPL, bool kCull, bool kRays = false>
 __global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() * 32 / kRefineMaxThreads) k_brefine(const __grid_constant__ BatchTable t,
                                                                   const __grid_constant__ RefineTable R, BatchGrids G,
                                                                   const char* __restrict__ bvh,
                                                                   const unsigned long long* __restrict__ bmask,
                                                                   const int32_t* __restrict__ blist,
+                                                                  int32_t* __restrict__ dlist,
                                                                   uint32_t* __restrict__ count,
                                                                   rtsdf_counters* counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmemT<RPL>& w = reinterpret_cast<WarpSmemT<RPL>*>(smem_raw)[warp];
-    const uint32_t nact = count[0];
+    const uint32_t nact = count[kRays ? 3 : 0];
     uint32_t n_hit = 0, n_fail = 0, n_ovf = 0;
     while (true) {
         uint32_t wk = 0;
-        if (lane == 0) wk = atomicAdd(count + 1, 1u);
+        if (lane == 0) wk = atomicAdd(count + (kRays ? 4 : 1), 1u);
         wk = __shfl_sync(0xffffffffu, wk, 0);
         if (wk >= nact) break;
-        const uint32_t e = (uint32_t)blist[wk];
+        const uint32_t e = (uint32_t)(kRays ? dlist[wk] : blist[wk]);
         const int si = (int)(e >> kBrickBits), b = (int)(e & ((1u << kBrickBits) - 1u));
         const SceneD& S = t.s[si];
         const RefineArgs& a = R.a[si];
@@ -328,11 +333,11 @@ __global__ void __launch_bounds__(kRefineMaxThreads, refine_warps_per_sm<RPL>() 
         const int n_inner = n_leaves > 1 ? n_leaves - 1 : 1;
         const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
         const int64_t o = S.vox_off;
-        refine_brick<BX, BY, BZ, false, RPL, false, kCull>(a, nodes, leaves, n_leaves, n_inner,
-                                                          (S.flood_b ? G.buf_b : G.buf_a) + o,
-                                        G.rep_tri + o, bmask[S.brick_off + b], bx, by, bz, G.dist_bits + o,
-                                        G.front + o, G.back + o, G.sdf + o, nullptr, nullptr, w, n_hit, n_fail,
-                                        n_ovf);
+        const bool deferred = refine_brick<BX, BY, BZ, false, RPL, false, kCull, kRays>(
+            a, nodes, leaves, n_leaves, n_inner, (S.flood_b ? G.buf_b : G.buf_a) + o, G.rep_tri + o,
+            bmask[S.brick_off + b], bx, by, bz, G.dist_bits + o, G.front + o, G.back + o, G.sdf + o, nullptr, nullptr,
+            w, n_hit, n_fail, n_ovf);
+        if (deferred && lane == 0) dlist[atomicAdd(count + 3, 1u)] = (int32_t)e;
     }
     if (counters) {
         if (n_hit) atomicAdd(&counters->rays_hit, n_hit);
@@ -383,7 +388,7 @@ struct rtsdf_batch_plan {
     // workspace layout (byte offsets)
     size_t off_keys = 0, off_counts = 0, off_offsets = 0, off_scan = 0;
     size_t off_k64a = 0, off_k64b = 0, off_va = 0, off_vb = 0, off_sort = 0, off_pin = 0, off_pl = 0, off_vis = 0;
-    size_t off_count = 0, off_bmask = 0, off_blist = 0, ws_bytes = 0;
+    size_t off_count = 0, off_bmask = 0, off_blist = 0, off_dlist = 0, ws_bytes = 0;
     // the captured JFA chain
     cudaGraphExec_t jfa_exec = nullptr;
     cudaStream_t capture_stream = nullptr;
@@ -536,15 +541,23 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     const BatchTable t = make_table(P, sh);
     RefineTable R;
     memset(&R, 0, sizeof(R));
-    for (int si = 0; si < t.n; ++si)
+    for (int si = 0; si < t.n; ++si) {
         R.a[si] = scene_args<BX, BY, BZ>(t.s[si], static_cast<const char*>(B.bvh), frame, accumulate);
+        // coarse scenes trace the rays of their overflowing bricks one by one
+        const rtsdf_batch_scene& sc = P.scenes[si];
+        R.a[si].per_ray = kCull && staged_estimate(sc.T, sc.grid.nx, sc.grid.ny, sc.grid.nz, sc.refine.max_ray_vox,
+                                                   BX, BY, BZ) >= per_ray_estimate(sc.refine.rays_per_voxel);
+    }
     char* ws = static_cast<char*>(B.ws);
     auto* count = reinterpret_cast<uint32_t*>(ws + P.off_count);
     auto* bmask = reinterpret_cast<unsigned long long*>(ws + P.off_bmask);
     auto* blist = reinterpret_cast<int32_t*>(ws + P.off_blist);
+    auto* dlist = reinterpret_cast<int32_t*>(ws + P.off_dlist);
+    bool per_ray = false;
+    for (int si = 0; si < t.n; ++si) per_ray = per_ray || R.a[si].per_ray != 0;
     BatchGrids G{B.seed, B.buf_b, B.rep_tri, B.dist_bits, B.front, B.back, B.sdf, B.verts, B.tris,
                  static_cast<const char*>(B.bvh)};
-    RTSDF_CUDA(cudaMemsetAsync(count, 0, 16, s));
+    RTSDF_CUDA(cudaMemsetAsync(count, 0, 32, s));
     k_bresolve<BX, BY, BZ><<<P.ntiles, 512, 0, s>>>(t, R, G, bmask, blist, count);
     RTSDF_LAUNCHED();
     const size_t smem = sizeof(WarpSmemT<RPL>) * (size_t)warps;
@@ -554,13 +567,24 @@ rtsdf_status launch_refine(const rtsdf_batch_plan& P, const rtsdf_batch_buffers&
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ, RPL, kCull>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(sizeof(WarpSmemT<RPL>) * 4)));
+        if constexpr (kCull)
+            RTSDF_CUDA(cudaFuncSetAttribute(k_brefine<BX, BY, BZ, RPL, kCull, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(WarpSmemT<RPL>) * 4)));
         attr_set[dev] = true;
     }
     // the same resident warps per SM for every CTA size (shared memory bound)
-    k_brefine<BX, BY, BZ, RPL, kCull><<<num_sms() * (refine_warps_per_sm<RPL>() / warps), 32 * warps, smem, s>>>(t, R, G,
-                                                                            static_cast<const char*>(B.bvh), bmask,
-                                                                            blist, count, counters);
+    const int ctas = num_sms() * (refine_warps_per_sm<RPL>() / warps);
+    k_brefine<BX, BY, BZ, RPL, kCull><<<ctas, 32 * warps, smem, s>>>(t, R, G, static_cast<const char*>(B.bvh), bmask,
+                                                                     blist, dlist, count, counters);
     RTSDF_LAUNCHED();
+    if constexpr (kCull) {
+        if (per_ray) {  // the bricks the first launch left to the per-ray walk
+            k_brefine<BX, BY, BZ, RPL, kCull, true><<<ctas, 32 * warps, smem, s>>>(
+                t, R, G, static_cast<const char*>(B.bvh), bmask, blist, dlist, count, counters);
+            RTSDF_LAUNCHED();
+        }
+    }
     if (counters) {
         int64_t nb = 0;
         for (int si = 0; si < P.S; ++si) nb += shape_bricks(P.scenes[si].grid, sh);
@@ -752,6 +776,7 @@ rtsdf_status rtsdf_batch_plan_create(const rtsdf_batch_scene* scenes, int32_t S,
     P->off_count = take(64);
     P->off_bmask = take(8 * (size_t)mb);
     P->off_blist = take(4 * (size_t)mb);
+    P->off_dlist = take(4 * (size_t)mb);
     P->ws_bytes = off;
     *plan = P;
     return RTSDF_OK;

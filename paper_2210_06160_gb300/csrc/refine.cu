@@ -18,7 +18,12 @@
 //             each ray (ties to the lower triangle id) lowers the voxel's distance
 //             and adds one front/back vote; the lane then writes the accumulated
 //             state and the signed value.  Staging runs in rounds when a brick has
-//             more candidates than the buffer holds.
+//             more candidates than the buffer holds.  On coarse grids (a staged-
+//             triangle estimate above a threshold that grows with the ray count)
+//             a brick whose walk overflows the list is left to a second launch
+//             instead, k_refine<..., kRays>, in which each ray walks the BVH on its
+//             own (slab tests, nearer child first, boxes beyond the closest hit so
+//             far skipped) and nothing is staged.
 #include "refine_core.cuh"
 #include "rtsdf_launch.cuh"
 
@@ -28,9 +33,11 @@ constexpr int kBX = 4, kBY = 4, kBZ = 4;  // brick shape of the single-scene pat
 constexpr int kRefineThreads = 64;        // two independent warps per CTA
 
 struct RefineWs {
-    uint32_t* count;            // [0] active bricks, [1] work counter, [2] walks that overflowed
+    uint32_t* count;            // [0] active bricks, [1] work counter, [2] walks that overflowed,
+                                // [3] bricks left to the per-ray launch, [4] its work counter
     unsigned long long* bmask;  // per brick: bit (lz*16 + ly*4 + lx) set for masked voxels
     int32_t* blist;             // active bricks
+    int32_t* dlist;             // bricks left to the per-ray launch
 };
 
 static size_t nbricks(const rtsdf_grid& g) {
@@ -48,10 +55,12 @@ static size_t refine_ws_layout(const rtsdf_grid& g, char* base, RefineWs* w) {
     char* c = take(64);
     char* m = take(8 * nb);
     char* l = take(4 * nb);
+    char* d = take(4 * nb);
     if (w) {
         w->count = reinterpret_cast<uint32_t*>(c);
         w->bmask = reinterpret_cast<unsigned long long*>(m);
         w->blist = reinterpret_cast<int32_t*>(l);
+        w->dlist = reinterpret_cast<int32_t*>(d);
     }
     return off;
 }
@@ -76,8 +85,10 @@ __global__ void __launch_bounds__(512, 4) k_resolve(RefineArgs a, const int32_t*
 
 // ------------------------------------------------------------------ refine
 
-// Persistent: warps take bricks from the work list until it is exhausted.
-template <bool kTrack, int RPL, bool kCount, bool kCull>
+// Persistent: warps take bricks from the work list until it is exhausted.  With kCull
+// the bricks that refine_brick leaves to the per-ray launch go to dlist; with kRays
+// the kernel is that launch and takes its bricks from dlist.
+template <bool kTrack, int RPL, bool kCount, bool kCull, bool kRays = false>
 __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 32 / kRefineThreads) k_refine(RefineArgs a, const BvhHeader* __restrict__ hdr,
                                                               const BvhNode* __restrict__ nodes,
                                                               const BvhLeaf* __restrict__ leaves,
@@ -85,6 +96,7 @@ __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 3
                                                               const int32_t* __restrict__ rep_tri,
                                                               const unsigned long long* __restrict__ bmask,
                                                               const int32_t* __restrict__ blist,
+                                                              int32_t* __restrict__ dlist,
                                                               uint32_t* __restrict__ count,
                                                               uint32_t* __restrict__ dist_bits,
                                                               uint32_t* __restrict__ front,
@@ -97,19 +109,20 @@ __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 3
     WarpSmemT<RPL>& w = reinterpret_cast<WarpSmemT<RPL>*>(smem_raw)[warp];
     const int n_leaves = hdr->n_leaves;
     const int n_inner = n_leaves > 1 ? n_leaves - 1 : 1;
-    const uint32_t nact = count[0];
+    const uint32_t nact = count[kRays ? 3 : 0];
     uint32_t n_hit = 0, n_fail = 0, n_ovf = 0;
     if (kCount) work_reset(w);
     while (true) {
         uint32_t wk = 0;
-        if (lane == 0) wk = atomicAdd(count + 1, 1u);
+        if (lane == 0) wk = atomicAdd(count + (kRays ? 4 : 1), 1u);
         wk = __shfl_sync(0xffffffffu, wk, 0);
         if (wk >= nact) break;
-        const int b = blist[wk];
+        const int b = kRays ? dlist[wk] : blist[wk];
         const int bx = b % a.nbx, by = (b / a.nbx) % a.nby, bz = b / (a.nbx * a.nby);
-        refine_brick<kBX, kBY, kBZ, kTrack, RPL, kCount, kCull>(a, nodes, leaves, n_leaves, n_inner, nearest, rep_tri, bmask[b], bx, by,
-                                            bz, dist_bits, front, back, sdf, win_ray, win_tri, w, n_hit, n_fail,
-                                            n_ovf);
+        const bool deferred = refine_brick<kBX, kBY, kBZ, kTrack, RPL, kCount, kCull, kRays>(
+            a, nodes, leaves, n_leaves, n_inner, nearest, rep_tri, bmask[b], bx, by, bz, dist_bits, front, back, sdf,
+            win_ray, win_tri, w, n_hit, n_fail, n_ovf);
+        if (deferred && lane == 0) dlist[atomicAdd(count + 3, 1u)] = b;
     }
     if (counters) {
         if (n_hit) atomicAdd(&counters->rays_hit, n_hit);
@@ -119,38 +132,44 @@ __global__ void __launch_bounds__(kRefineThreads, refine_warps_per_sm<RPL>() * 3
     if (lane == 0 && n_ovf) atomicAdd(count + 2, n_ovf);
 }
 
-template <bool kTrack, int RPL, bool kCount, bool kCull>
+template <bool kTrack, int RPL, bool kCount, bool kCull, bool kRays = false>
 static rtsdf_status launch_refine_t(cudaStream_t s, const RefineArgs& a, const BvhHeader* hdr,
                                     const BvhNode* nodes, const BvhLeaf* leaves, const int32_t* nearest,
                                     const int32_t* rep_tri, const unsigned long long* bmask, const int32_t* blist,
-                                    uint32_t* count, uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
+                                    int32_t* dlist, uint32_t* count, uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
                                     rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
     const size_t smem = sizeof(WarpSmemT<RPL>) * (kRefineThreads / 32);
     static bool attr_set[64] = {};
     int dev = 0;
     RTSDF_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RTSDF_CUDA(cudaFuncSetAttribute(k_refine<kTrack, RPL, kCount, kCull>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+        RTSDF_CUDA(cudaFuncSetAttribute(k_refine<kTrack, RPL, kCount, kCull, kRays>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set[dev] = true;
     }
-    k_refine<kTrack, RPL, kCount, kCull><<<num_sms() * (refine_warps_per_sm<RPL>() * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
-        a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, count, dist_bits, front, back, sdf, counters, win_ray,
-        win_tri);
+    k_refine<kTrack, RPL, kCount, kCull, kRays>
+        <<<num_sms() * (refine_warps_per_sm<RPL>() * 32 / kRefineThreads), kRefineThreads, smem, s>>>(
+            a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, dlist, count, dist_bits, front, back, sdf, counters,
+            win_ray, win_tri);
     return RTSDF_OK;
 }
 
-static rtsdf_status launch_refine_kernel(bool track, bool count, bool cull, int rpl, cudaStream_t s,
+static rtsdf_status launch_refine_kernel(bool track, bool count, bool cull, bool rays, int rpl, cudaStream_t s,
                                          const RefineArgs& a, const BvhHeader* hdr, const BvhNode* nodes,
                                          const BvhLeaf* leaves, const int32_t* nearest, const int32_t* rep_tri,
-                                         const unsigned long long* bmask, const int32_t* blist, uint32_t* wcount,
+                                         const unsigned long long* bmask, const int32_t* blist, int32_t* dlist,
+                                         uint32_t* wcount,
                                          uint32_t* dist_bits, uint32_t* front, uint32_t* back, float* sdf,
                                          rtsdf_counters* counters, uint32_t* win_ray, int32_t* win_tri) {
 #define RTSDF_REFINE_CASE(T, R, N, C)                                                                           \
-    if (track == T && rpl == R && count == N && cull == C)                                                      \
-        return launch_refine_t<T, R, N, C>(s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, wcount,    \
-                                           dist_bits, front, back, sdf, counters, T ? win_ray : nullptr,        \
-                                           T ? win_tri : nullptr);
+    if (track == T && rpl == R && count == N && cull == C && !rays)                                             \
+        return launch_refine_t<T, R, N, C>(s, a, hdr, nodes, leaves, nearest, rep_tri, bmask, blist, dlist,     \
+                                           wcount, dist_bits, front, back, sdf, counters, T ? win_ray : nullptr, \
+                                           T ? win_tri : nullptr);                                               \
+    if (!T && C && track == T && rpl == R && count == N && rays)                                                \
+        return launch_refine_t<false, R, N, true, true>(s, a, hdr, nodes, leaves, nearest, rep_tri, bmask,      \
+                                                        blist, dlist, wcount, dist_bits, front, back, sdf,      \
+                                                        counters, nullptr, nullptr);
     RTSDF_REFINE_CASE(false, 2, false, false) RTSDF_REFINE_CASE(false, 4, false, false)
     RTSDF_REFINE_CASE(false, 8, false, false) RTSDF_REFINE_CASE(false, 16, false, false)
     RTSDF_REFINE_CASE(true, 2, false, false) RTSDF_REFINE_CASE(true, 4, false, false)
@@ -203,13 +222,14 @@ rtsdf_status refine(const rtsdf_grid& gh, int32_t T, const void* bvh, const int3
     a.nbx = (gh.nx + kBX - 1) / kBX;
     a.nby = (gh.ny + kBY - 1) / kBY;
     a.nbz = (gh.nz + kBZ - 1) / kBZ;
+    a.per_ray = 0;
     RefineWs w;
     refine_ws_layout(gh, static_cast<char*>(ws), &w);
     const auto* hdr = static_cast<const BvhHeader*>(bvh);
     const auto* nodes = reinterpret_cast<const BvhNode*>(static_cast<const char*>(bvh) + bvh_nodes_offset());
     const auto* leaves = reinterpret_cast<const BvhLeaf*>(static_cast<const char*>(bvh) + bvh_leaves_offset(T));
     a.tv = reinterpret_cast<const TriVox*>(static_cast<const char*>(bvh) + bvh_tris_offset(T));
-    RTSDF_CUDA(cudaMemsetAsync(w.count, 0, 16, s));
+    RTSDF_CUDA(cudaMemsetAsync(w.count, 0, 32, s));
     const dim3 rgrid((gh.nx + 31) / 32, (gh.ny + 3) / 4, (gh.nz + 3) / 4);
     const bool track = win_ray != nullptr;
     k_resolve<<<rgrid, 512, 0, s>>>(a, nearest, rep_tri, dist_bits, front, back, sdf, w.bmask, w.blist, w.count,
@@ -220,10 +240,19 @@ rtsdf_status refine(const rtsdf_grid& gh, int32_t T, const void* bvh, const int3
     const bool count_work = !track && counters != nullptr && p.count_work != 0;
     // coarse grids (many triangles within a brick's reach) take the culling instantiation;
     // tracked calls (the adjoint's forward) keep the plain one
-    const bool cull = !track && staged_estimate(T, gh.nx, gh.ny, gh.nz, a.tmax, kBX, kBY, kBZ) >= kCullEstimate;
-    RTSDF_TRY(launch_refine_kernel(track, count_work, cull, rpl, s, a, hdr, nodes, leaves, nearest, rep_tri, w.bmask, w.blist,
-                                   w.count, dist_bits, front, back, sdf, counters, win_ray, win_tri));
+    const double est = staged_estimate(T, gh.nx, gh.ny, gh.nz, a.tmax, kBX, kBY, kBZ);
+    const bool cull = !track && est >= kCullEstimate;
+    a.per_ray = cull && est >= per_ray_estimate(a.R) ? 1 : 0;
+    RTSDF_TRY(launch_refine_kernel(track, count_work, cull, false, rpl, s, a, hdr, nodes, leaves, nearest, rep_tri,
+                                   w.bmask, w.blist, w.dlist, w.count, dist_bits, front, back, sdf, counters, win_ray,
+                                   win_tri));
     RTSDF_LAUNCHED();
+    if (a.per_ray) {  // the bricks the first launch left to the per-ray walk
+        RTSDF_TRY(launch_refine_kernel(track, count_work, cull, true, rpl, s, a, hdr, nodes, leaves, nearest, rep_tri,
+                                       w.bmask, w.blist, w.dlist, w.count, dist_bits, front, back, sdf, counters,
+                                       win_ray, win_tri));
+        RTSDF_LAUNCHED();
+    }
     if (counters) {
         k_refine_report<<<num_sms(), 256, 0, s>>>(w.count, w.bmask, nbricks(gh), counters);
         RTSDF_LAUNCHED();

@@ -30,6 +30,13 @@ inline double staged_estimate(int T, int nx, int ny, int nz, float tmax, int bx,
     const double f = ((double)bx + e) * ((double)by + e) * ((double)bz + e) / ((double)nx * ny * nz);
     return (double)T * (f < 1.0 ? f : 1.0);
 }
+// Staged-triangle estimate from which a launch (or a batch's scene) with R rays per
+// voxel traces the rays of its overflowing bricks through the BVH one by one
+// (ray_closest) instead of staging: the staged path costs about the same per staged
+// triangle whatever R, the per-ray walk a fixed amount per ray, so the crossover grows
+// with R (measured on the room at 128x64x128: 1 ray 3.0 -> 0.58 ms, 5 rays 3.65 ->
+// 2.36 ms, 10 rays 4.5 -> 6.0 ms, at an estimate of 830).
+inline double per_ray_estimate(int R) { return 150.0 + 100.0 * (double)(R > 1 ? R - 1 : 0); }
 constexpr int kRefineMaxThreads = 128;                // refine CTAs hold 1, 2 or 4 warps
 constexpr int kRefineWarpsPerSm = 20;                 // resident refine warps per SM (shared memory bound)
 constexpr int kRefineWarpsPerSm16 = 12;               // the same with 16-ray groups (twice the ray rows)
@@ -56,6 +63,7 @@ struct RefineArgs {
     int nbx, nby, nbz;  // brick grid
     int ratio;          // fine voxels per coarse voxel along each axis (1: one grid)
     int cnx, cny, cnz;  // coarse grid of the flooded seeds and representative triangles
+    int per_ray;        // culling instantiation: overflowing bricks go to the per-ray launch
 };
 
 constexpr int kMaxBricksPerTile = 16;
@@ -364,6 +372,111 @@ __device__ __forceinline__ void run_items(WarpSmemT<RPL>& w, const BvhLeaf* __re
     }
 }
 
+// Slab test of a ray against box [lo, hi]: iv the inverse direction components, no =
+// -o * iv, so the box's planes are crossed at t = lo * iv + no.  tn receives the entry
+// parameter (at least -1e-3); the box counts as hit when the entry is at most the exit
+// and at most lim, each with 1e-3 (voxel lengths; d is a unit vector) to spare.
+__device__ __forceinline__ bool ray_box(float4 lo, float4 hi, float3 iv, float3 no, float lim, float& tn) {
+    const float ax = __fmaf_rn(lo.x, iv.x, no.x), bx = __fmaf_rn(hi.x, iv.x, no.x);
+    const float ay = __fmaf_rn(lo.y, iv.y, no.y), by = __fmaf_rn(hi.y, iv.y, no.y);
+    const float az = __fmaf_rn(lo.z, iv.z, no.z), bz = __fmaf_rn(hi.z, iv.z, no.z);
+    tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), -1e-3f));
+    const float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+    return tn <= tf + 1e-3f && tn <= lim;
+}
+
+constexpr int kRayStack = 64;  // per-lane traversal stack: a radix tree over unique 64-bit keys is at most 64 deep
+
+// Closest hit of one ray (origin o, unit direction d, length tmax) over the whole
+// BVH, by a depth-first walk of the lane's own: both child boxes of a node get the
+// slab test, the nearer child is entered and the other pushed, and each leaf gets
+// the exact test of run_item (the same function, operands and key), so `best` is the
+// lowest key over all triangles, the one the staged path finds.  The boxes carry
+// the builder's padding (at least 1/64 voxel), far above the FP32 rounding of the
+// slab parameters (about 1e-7 of the coordinates) and of any accepted hit point, so
+// no box holding a hit is skipped; directions are kept at least 1e-12 from zero in
+// each component, which keeps every parameter finite and moves the ray by far less
+// than that padding.  Without kCount a box entered beyond the closest hit so far is
+// skipped (a hit inside it lies at or beyond its entry, so its key is not lower);
+// with kCount every box within the ray's length is opened, so that, as in the
+// staged path, the exact test sees every triangle the ray can hit and the near-edge
+// count covers every hit.  Returns false if the stack or the step guard would
+// overflow, which a tree from the builder never does; the caller counts the brick
+// like a walk that overflowed.
+template <bool kCount>
+__device__ __forceinline__ bool ray_closest(const BvhNode* __restrict__ nodes, const BvhLeaf* __restrict__ leaves,
+                                            int n_leaves, int n_inner, float3 o, float3 d, float tmax,
+                                            unsigned long long& best, uint32_t& box_tests, uint32_t& exact,
+                                            uint32_t& near) {
+    int stk[kRayStack];
+    float stn[kRayStack];
+    const float tiny = 1e-12f;
+    const float3 iv = make_float3(__frcp_rn(fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+                                  __frcp_rn(fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+                                  __frcp_rn(fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    const float3 no = make_float3(-o.x * iv.x, -o.y * iv.y, -o.z * iv.z);
+    best = ~0ull;
+    if (n_leaves <= 0) return true;
+    float lim = tmax * 1.000001f + 1e-3f;  // boxes entered beyond lim hold no lower key
+    int sp = 0, node = 0, guard = 0;
+    auto leaf = [&](int j) {
+        const BvhLeaf* L = leaves + j;
+        const float4 v0 = __ldg(&L->v0), e1f = __ldg(&L->e1), e2f = __ldg(&L->e2);
+        float t, margin;
+        bool front;
+        const bool hit = ray_tri_flat(o, d, make_float3(v0.x, v0.y, v0.z), make_float3(e1f.x, e1f.y, e1f.z),
+                                      make_float3(e2f.x, e2f.y, e2f.z), tmax, t, front, margin);
+        if (kCount) {
+            ++exact;
+            near += (hit && margin < 1e-6f) ? 1u : 0u;
+        }
+        if (hit) {
+            const uint32_t id = (uint32_t)__float_as_int(v0.w);
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)((id << 1) | (front ? 1u : 0u));
+            if (key < best) {
+                best = key;
+                if (!kCount) lim = t * 1.000001f + 1e-3f;
+            }
+        }
+    };
+    while (true) {
+        if (++guard > n_inner + 1) return false;  // a tree's walk enters each inner node once
+        const BvhNode* nd = nodes + node;
+        const float4 lo0 = __ldg(&nd->lo0), hi0 = __ldg(&nd->hi0), lo1 = __ldg(&nd->lo1), hi1 = __ldg(&nd->hi1);
+        const int c0 = __float_as_int(lo0.w), c1 = __float_as_int(hi0.w);
+        float t0 = 0.f, t1 = 0.f;
+        bool h0 = ray_box(lo0, hi0, iv, no, lim, t0) && (c0 >= 0 ? c0 < n_inner : ~c0 < n_leaves);
+        bool h1 = n_leaves > 1 && ray_box(lo1, hi1, iv, no, lim, t1) && (c1 >= 0 ? c1 < n_inner : ~c1 < n_leaves);
+        if (kCount) box_tests += n_leaves > 1 ? 2u : 1u;
+        if (h0 && c0 < 0) {
+            leaf(~c0);
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            leaf(~c1);
+            h1 = false;
+        }
+        if (h0 && h1) {
+            if (sp >= kRayStack) return false;
+            const bool n0 = t0 <= t1;
+            stk[sp] = n0 ? c1 : c0;
+            stn[sp] = n0 ? t1 : t0;
+            ++sp;
+            node = n0 ? c0 : c1;
+        } else if (h0 || h1) {
+            node = h0 ? c0 : c1;
+        } else {
+            // pop the next pushed node still entered within lim
+            do {
+                if (sp == 0) return true;
+                --sp;
+            } while (stn[sp] > lim);
+            node = stk[sp];
+        }
+    }
+}
+
 // Which rays of one (voxel slot v, staged triangle) pair can hit the triangle.  Two
 // necessary conditions, each a dot product of the ray direction d with a per-pair
 // vector against a per-pair threshold:
@@ -559,6 +672,30 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, int n) {
     return pos;
 }
 
+// Lists the (slot, ray) items of the warp's rays in its item queue, which holds
+// 32 * RPL of them: bit r of m in lane l gives item (l << 5) | r, lanes in order.
+// Returns the number of items; called by the whole warp.
+template <int RPL>
+__device__ __forceinline__ int list_rays(WarpSmemT<RPL>& w, uint32_t m) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(m);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - cnt;
+    while (m) {
+        const int r = __ffs(m) - 1;
+        m &= m - 1u;
+        w.queue[pos++] = ((uint32_t)lane << 5) | (uint32_t)r;
+    }
+    __syncwarp();
+    return total;
+}
+
 // Rays of the group whose first draw failed (both candidate pairs of attempt 0
 // rejected, about 4.6% of rays; bit r of `need` in the lane owning the slot) continue
 // from attempt 1, one ray per lane: the warp lists its (slot, ray) items in the item
@@ -570,21 +707,7 @@ template <int RPL>
 __device__ __forceinline__ void redraw(WarpSmemT<RPL>& w, uint32_t need, const RefineArgs& a, int r0,
                                        uint32_t& n_fail) {
     const int lane = threadIdx.x & 31;
-    const int cnt = __popc(need);
-    int incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int pos = incl - cnt;
-    while (need) {
-        const int r = __ffs(need) - 1;
-        need &= need - 1u;
-        w.queue[pos++] = ((uint32_t)lane << 5) | (uint32_t)r;
-    }
-    __syncwarp();
+    const int total = list_rays<RPL>(w, need);
     for (int b = 0; b < total; b += 32) {
         if (b + lane < total) {
             const uint32_t it = w.queue[b + lane];
@@ -621,8 +744,15 @@ __device__ __forceinline__ void redraw(WarpSmemT<RPL>& w, uint32_t need, const R
 // multiply-adds because they decide nothing the oracle decides.
 // RPL: rays per lane and group (2, 4 or 8); calls with R <= RPL rays per voxel run
 // one group, so small ray counts do not pay for eight.
-template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane, bool kCount = false, bool kCull = false>
-__device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode* __restrict__ nodes,
+// With kCull and a.per_ray, a brick whose walk overflows its list (more than
+// kListCap - 64 triangles within reach of its rays) is not refined here: the call
+// returns true and the caller lists the brick for a second launch with kRays, in
+// which every ray of the brick walks the BVH on its own (ray_closest) and nothing
+// is staged.  The two paths live in separate kernels so that the staged one keeps
+// its registers.
+template <int BX, int BY, int BZ, bool kTrack, int RPL = kRaysPerLane, bool kCount = false, bool kCull = false,
+          bool kRays = false>
+__device__ __forceinline__ bool refine_brick(const RefineArgs& a, const BvhNode* __restrict__ nodes,
                                              const BvhLeaf* __restrict__ leaves, int n_leaves, int n_inner,
                                              const int32_t* __restrict__ nearest,
                                              const int32_t* __restrict__ rep_tri, unsigned long long m, int bx,
@@ -643,17 +773,19 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
     // walk once for the whole brick; the list is reused by every pass and ray
     // group unless it overflowed, in which case each pass walks again in rounds
     int sp0 = 0;
-    if (n_leaves > 0) {
+    if (!kRays && n_leaves > 0) {
         if (lane == 0) w.stack[0] = 0;
         sp0 = 1;
     }
     __syncwarp();
     BrickWork bw;
     uint32_t box_tests = 0;
-    const int nc_all = walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack, sp0, w.list, 0,
-                                      overflow, box_tests);
+    const int nc_all = kRays ? 0
+                             : walk_and_stage(nodes, n_inner, n_leaves, qlo, qhi, ext * ext, w.stack, sp0, w.list, 0,
+                                              overflow, box_tests);
     if (kCount) work_add(w, kWorkNodes, box_tests);
-    const bool complete = sp0 == 0;
+    const bool complete = !kRays && sp0 == 0;
+    if (kCull && !kRays && a.per_ray && !complete) return true;  // for the per-ray launch
     for (int pass = 0; pass * 32 < nm; ++pass) {
         const int slot = pass * 32 + lane;
         const bool mine = slot < nm;
@@ -705,13 +837,42 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
             }
             w.okm[lane] = okm;
             if (__any_sync(0xffffffffu, need != 0u)) redraw<RPL>(w, need, a, r0, n_fail);
+            __syncwarp();
+            bool staged = !kRays;
+            if (kRays) {
+                // the pass's rays, 32 at a time over the lanes whatever their voxels
+                bool done = true;
+                uint32_t nb = 0, ne = 0, nn = 0;
+                const int total = list_rays<RPL>(w, w.okm[lane]);
+                for (int b = 0; b < total; b += 32) {
+                    if (b + lane < total) {
+                        const uint32_t it = w.queue[b + lane];
+                        const int sl = (int)(it >> 5), r = (int)(it & 31u);
+                        const float4 of = w.origin[sl];
+                        const float3 dd = make_float3(dq_comp(w, 0, r, sl), dq_comp(w, 1, r, sl),
+                                                      dq_comp(w, 2, r, sl));
+                        unsigned long long key;
+                        done = ray_closest<kCount>(nodes, leaves, n_leaves, n_inner, make_float3(of.x, of.y, of.z),
+                                                   dd, a.tmax, key, nb, ne, nn) && done;
+                        w.key[r][sl] = key;
+                    }
+                }
+                if (kCount) {
+                    work_add(w, kWorkNodes, __reduce_add_sync(0xffffffffu, nb));
+                    bw.exact += __reduce_add_sync(0xffffffffu, ne);
+                    bw.near += __reduce_add_sync(0xffffffffu, nn);
+                }
+                // a malformed tree (never built): counted like a walk that overflowed
+                if (!done) overflow = true;
+                __syncwarp();
+            }
             int sp = 0;
-            if (!complete && n_leaves > 0) {
+            if (staged && !complete && n_leaves > 0) {
                 if (lane == 0) w.stack[0] = 0;
                 sp = 1;
             }
             __syncwarp();
-            bool first = true;
+            bool first = staged;
             while (first || sp > 0) {
                 first = false;
                 box_tests = 0;
@@ -842,7 +1003,8 @@ __device__ __forceinline__ void refine_brick(const RefineArgs& a, const BvhNode*
         w.work[kWorkExact] += bw.exact;
         w.near_edge += bw.near;
     }
-    n_ovf += overflow ? 1u : 0u;
+    n_ovf += __any_sync(0xffffffffu, overflow) ? 1u : 0u;
+    return false;
 }
 
 }  // namespace rtsdf

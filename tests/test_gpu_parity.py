@@ -47,15 +47,25 @@ def test_small_room_accumulated_frames_parity():
     assert np.abs(vis - vis_ref).max() <= SHADOW_TOL
 
 
-def test_coarse_grid_parity():
+@pytest.mark.parametrize("count_work", [True, False])
+def test_coarse_grid_parity(count_work):
     """The small room on a 24x12x24 grid: the 8-voxel rays span a third of the scene,
-    so every brick stages most of the mesh and the refinement takes its culling form
-    (whole chunks of staged triangles skipped for voxels whose rays miss their
-    bounding sphere); the field must still equal the oracle's, whole grid, two
+    so every brick has far more triangles within reach than its staging list holds
+    and the refinement traces each ray through the BVH on its own (uncounted: boxes
+    entered beyond the closest hit so far are skipped; counted: every box within the
+    ray's length is opened); the field must still equal the oracle's, whole grid, two
     accumulated frames."""
     sc = scenes.scene_small_room(n=24)
     ref = oracle.rebuild(sc)
-    got, _ = gpu_rebuild(sc)
+    got, _ = gpu_rebuild(sc, count_work=count_work)
+    if count_work:
+        # bricks whose walk overflowed (most of the 1,178 triangles within reach) stage
+        # nothing; the others stage at most 256, so reach tests stay below 256 per voxel
+        c = got["counters"]
+        assert 0 < c["reach_tests"] <= 256 * c["masked_voxels"] or c["reach_tests"] == 0, c
+        assert c["exact_tests"] > 0, c
+    else:
+        del got["counters"]  # the uncounted kernels count no near-edge hits
     compare_rebuild(ref, got)
 
 
