@@ -82,6 +82,28 @@ def test_small_batch_matches_oracle_and_single_scene_builds():
     assert c["rays_failed"] == 0 and c["stack_overflow"] == 0
 
 
+def test_coarse_scene_in_a_batch_matches_oracle():
+    """A coarse scene (the small room on 24x12x24: most of its 1,178 triangles lie within
+    reach of every brick, so each brick's walk overflows the staging list and the
+    batch's per-ray launch refines it) batched with a fine one: both against the
+    oracle and against their single-scene builds (whose per-ray walk counts its work
+    and so opens every box, where the batch skips boxes beyond the closest hit)."""
+    coarse = dataclasses.replace(scenes.scene_small_room(n=24), frames=1)
+    coarse = dataclasses.replace(coarse, refine=dataclasses.replace(coarse.refine, accumulate=False))
+    scs = [coarse, scenes.scene_batch_small()[3]]
+    B = rt.Batch(scs)
+    B.rebuild(0, False)
+    torch.cuda.synchronize()
+    for i, sc in enumerate(scs):
+        got = _batch_scene_arrays(B, i)
+        ref = oracle.rebuild(sc)
+        m = ref["mask"].astype(bool)
+        _assert_same(got, ref, m, sc.name + " vs oracle", sdf_tol=1e-5)
+        _assert_same(got, _plain(sc), m, sc.name + " vs single-scene")
+    c = rt.counters_dict(B.counters)
+    assert c["rays_failed"] == 0 and c["stack_overflow"] == 0
+
+
 def test_every_tuning_gives_the_same_bits():
     scs = scenes.scene_batch_small()
     B = rt.Batch(scs)
