@@ -19,6 +19,10 @@ launch ends quickly while the kernel sees the benchmark's voxel size and scene.
         rtsdf_backward calls (65,536 samples, 512x512 shadow image)
     python -m paper_2210_06160_gb300.profile_cases batch
         the 48-scene batch (118.8 M voxels): two batched rebuilds
+    python -m paper_2210_06160_gb300.profile_cases refine-coarse
+        the room on a 128x64x128 grid with 5 rays per voxel, three fresh frames:
+        each refinement is two k_refine launches, the staged one (which leaves
+        the bricks whose walk overflows to the next) and the per-ray walk
 """
 from __future__ import annotations
 
@@ -65,6 +69,17 @@ def case_refine_subbox(frames: int = 3) -> None:
     c1 = rt.counters_dict(P.counters)
     work = {k: c1[k] - c0[k] for k in ("masked_voxels", "node_tests", "reach_tests", "filter_pairs", "exact_tests")}
     print("refine-subbox ok", work)
+
+
+def case_refine_coarse(frames: int = 3) -> None:
+    sc = scenes.scene_room(nx=128, ny=64, nz=128, shadow_w=64, shadow_h=36)
+    v, t = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tris).cuda()
+    P = rt.Pipeline(sc.grid, len(sc.verts), len(sc.tris))
+    rp = dataclasses.replace(sc.refine, rays_per_voxel=5, accumulate=False)
+    for f in range(frames):
+        P.rebuild(v, t, sc.jfa_steps, rt.make_refine_params(dataclasses.replace(rp, frame_index=f)))
+    torch.cuda.synchronize()
+    print("refine-coarse ok", rt.counters_dict(P.counters))
 
 
 def case_shadow(coherent: bool = False) -> None:
@@ -134,6 +149,8 @@ if __name__ == "__main__":
         case_adjoint()
     elif which == "batch":
         case_batch()
+    elif which == "refine-coarse":
+        case_refine_coarse()
     elif which == "refine-subbox":
         case_refine_subbox(int(sys.argv[2]) if len(sys.argv) > 2 else 3)
     else:
